@@ -1,0 +1,151 @@
+/*
+ * dsnufft.h -- C ABI of the GB300 (sm_103a) split nonlocal potential solver.
+ *
+ * Operation (Mauser, Stimming, Zhang, "A novel nonlocal potential solver based
+ * on nonuniform FFT for efficient simulation of the Davey-Stewartson
+ * equations", Sec. 2.1):
+ *
+ *     Phi = F^-1[ -k_x^2 / |k|^2  rho_hat ]           (eqs. Def_Fourier, FourTransDef)
+ *         = I1 + I2                                   (eqs. PotSplitWhoSpace, SubInt1, SubInt2)
+ *
+ *   I1: zero-padded (kappa = 2) uniform FFT of rho, multiplied by
+ *       (1 - p(k)) (-k_x^2/|k|^2), inverse FFT, restricted to the grid.
+ *   I2: polar Gauss quadrature over the disk |k| <= P (eq. I2PolarDisc):
+ *       rho_hat at radial Gauss-Legendre x uniform angular nodes by a type-2
+ *       NUFFT (eq. 2.2), weights -cos^2(theta) r w_r w_theta p(r) (2 pi)^-2,
+ *       and a type-1 NUFFT back onto the grid (eq. 2.1).
+ *   p(k) = exp(-|k|^2 / sigma^2) (Sec. 2.1).  Frequencies are angular
+ *   (rad/length); the grid is x_n = -L + n h, n = 0..N-1, h = 2L/N, periodic.
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are row-major [ny][nx] (x fastest), i.e. a (ny, nx) tensor.
+ *   - Pointers named *_dev are DEVICE pointers; the caller owns them.
+ *   - Calls that take a stream enqueue work on it and return at once
+ *     (stream == NULL means the legacy default stream).  No call synchronises
+ *     the device except dsnu_plan_create (final table upload) and
+ *     dsnu_status_poll.
+ *   - Errors: every call returns a dsnu_status.  Invalid arguments give
+ *     DSNU_EINVAL before any launch.  dsnu_last_error() returns a
+ *     thread-local message for the last failing call on this thread.
+ *     Nothing exits the process and nothing throws across the ABI.
+ */
+#ifndef DSNUFFT_H
+#define DSNUFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DSNU_OK = 0,
+  DSNU_EINVAL = 1,        /* invalid argument (nothing was launched) */
+  DSNU_ENOMEM = 2,        /* a plan table allocation failed */
+  DSNU_ECUDA = 3,         /* a CUDA runtime call failed; see dsnu_last_error() */
+  DSNU_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+  DSNU_EUNSUPPORTED = 5   /* valid request outside what this build supports */
+} dsnu_status;
+
+typedef enum {
+  DSNU_FP64 = 0,   /* every step in FP64 */
+  DSNU_MIXED = 1   /* FFT butterflies, ES spreading/interpolation in FP32;
+                      nodes, weights, twiddle/phase tables generated in FP64;
+                      the per-node low-frequency weighting in FP64;
+                      rho in and Phi out are FP64 */
+} dsnu_precision;
+
+typedef enum {
+  DSNU_PARTITION_GAUSS = 0,  /* p(k) = exp(-|k|^2/sigma^2) (Sec. 2.1) */
+  DSNU_PARTITION_SHARP = 1   /* p(k) = 1 on |k| <= P, 0 outside */
+} dsnu_partition;
+
+/* Solver parameters (Sec. 2.1).  Zero-valued optional fields take defaults. */
+typedef struct {
+  int32_t nx, ny;          /* grid points per axis: powers of two, 16..4096 */
+  double  lx, ly;          /* half-widths: domain [-lx,lx) x [-ly,ly), h = 2l/n */
+  double  cut_radius;      /* P: disk radius of the polar part, rad/length.
+                              Needs P*h + w*pi/(2n) < pi on both axes so that
+                              the disk plus the ES stencil lies inside the
+                              padded frequency grid. */
+  double  sigma;           /* partition width; 0 => P/6 (p(P) = e^-36) */
+  int32_t n_r, n_theta;    /* radial Gauss-Legendre x uniform angular nodes;
+                              n_theta even (node set symmetric under k -> -k) */
+  int32_t kernel_width;    /* ES kernel width w in fine-grid cells, 2..16;
+                              0 => 15 (FP64) or 8 (MIXED) */
+  int32_t pad_factor;      /* kappa; 0 or 2 (only 2 is supported) */
+  int32_t precision;       /* dsnu_precision */
+  int32_t partition;       /* dsnu_partition */
+} dsnu_params;
+
+typedef struct dsnu_plan_s* dsnu_plan;
+
+/* Build a plan: validates params, computes (FP64, on the host) the polar
+ * Gauss nodes and weights, the ES kernel weights of every node, the
+ * deconvolution and multiplier tables and the twiddle tables, bins the nodes
+ * into spreading tiles, and uploads the tables with cudaMemcpyAsync on
+ * `stream` (cudaStream_t, may be NULL), then synchronises that stream.
+ * Ownership: the plan owns its tables (device memory, freed by
+ * dsnu_plan_destroy); it does not own the workspace.
+ * Errors: DSNU_EINVAL (bad params, *out untouched), DSNU_ENOMEM, DSNU_ECUDA. */
+dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan* out);
+
+/* Bytes of device scratch one solve needs (intermediate spectra).  0 on a
+ * NULL plan. */
+size_t dsnu_workspace_bytes(dsnu_plan plan);
+
+/* Attach caller-owned device scratch of at least dsnu_workspace_bytes(plan)
+ * bytes, 256-byte aligned.  The plan keeps the pointer until it is replaced
+ * or the plan is destroyed; the caller must keep the memory alive and must
+ * not run two solves of the same plan concurrently (they share it).
+ * Errors: DSNU_EINVAL (NULL plan/pointer, too small, misaligned). */
+dsnu_status dsnu_set_workspace(dsnu_plan plan, void* workspace_dev, size_t bytes);
+
+/* Phi = I1 + I2 (Sec. 2.1, eq. PotSplitWhoSpace) for one density.
+ * rho_dev: [ny][nx] FP64 density (device, read only).
+ * phi_dev: [ny][nx] FP64 potential (device, written); must not alias rho_dev.
+ * Enqueued on `stream` (cudaStream_t or NULL).
+ * Errors: DSNU_EINVAL (NULL/aliased pointers, no workspace), DSNU_ECUDA (a
+ * launch failed). */
+dsnu_status dsnu_solve(dsnu_plan plan, const double* rho_dev, double* phi_dev, void* stream);
+
+/* Transpose of the discrete operator of dsnu_solve: the same pipeline with
+ * every transform conjugated, i.e. the transposed type-1/type-2 pair (type-1
+ * of the transpose = type-2 with e^{+i k.x}, and the reverse) around the same
+ * real weights, and the transposed padded FFT part.  The operator is
+ * symmetric (real even multiplier, node set symmetric under k -> -k), so the
+ * result equals dsnu_solve(g) up to rounding.  Same layout, ownership and
+ * errors as dsnu_solve. */
+dsnu_status dsnu_solve_adjoint(dsnu_plan plan, const double* g_dev, double* out_dev, void* stream);
+
+/* Read and clear the plan's device status word (written by bounded device
+ * waits); synchronises `stream`.  Returns DSNU_OK or the recorded status. */
+dsnu_status dsnu_status_poll(dsnu_plan plan, void* stream);
+
+/* Free the plan's tables.  The caller must make sure no work that uses the
+ * plan is still in flight.  NULL is accepted (DSNU_OK). */
+dsnu_status dsnu_plan_destroy(dsnu_plan plan);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* dsnu_last_error(void);
+
+/* Plan introspection for tests and benchmarks (host values, no device work). */
+typedef struct {
+  int32_t n_nodes;       /* n_r * n_theta */
+  int32_t band_q;        /* Q: band half-width in fine-grid cells */
+  int32_t kernel_width;  /* resolved ES width */
+  int32_t precision;
+  double  sigma;         /* resolved partition width */
+  double  es_beta;       /* ES shape parameter */
+  int32_t n_tiles;       /* spreading tiles */
+  int32_t max_tile_nodes;
+} dsnu_plan_info;
+
+dsnu_status dsnu_plan_get_info(dsnu_plan plan, dsnu_plan_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSNUFFT_H */

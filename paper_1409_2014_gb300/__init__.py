@@ -1,0 +1,113 @@
+"""GB300 (sm_103a) split nonlocal potential solver for the Davey-Stewartson
+equations: Phi = F^-1[-k_x^2/|k|^2 rho_hat] evaluated as I1 (zero-padded FFT,
+high frequencies) + I2 (polar Gauss quadrature via type-2 / type-1 NUFFTs),
+after Mauser, Stimming, Zhang (Sec. 2.1).
+
+The compute runs in the C-ABI library ``libdsnufft.so`` (include/dsnufft.h);
+this module only marshals arguments.  PyTorch supplies device memory and
+streams.
+"""
+
+from __future__ import annotations
+
+from . import _abi
+from ._abi import (  # noqa: F401
+    DSNU_FP64, DSNU_MIXED, DSNU_PARTITION_GAUSS, DSNU_PARTITION_SHARP, DsnuError,
+    dsnu_last_error, dsnu_params, dsnu_plan_create, dsnu_plan_destroy, dsnu_plan_get_info,
+    dsnu_set_workspace, dsnu_solve, dsnu_solve_adjoint, dsnu_status_poll, dsnu_workspace_bytes,
+)
+
+_PREC = {"fp64": DSNU_FP64, "mixed": DSNU_MIXED}
+_PART = {"gauss": DSNU_PARTITION_GAUSS, "sharp": DSNU_PARTITION_SHARP}
+
+
+def make_params(nx, ny, lx, ly, cut_radius, n_r, n_theta, sigma=0.0, kernel_width=0,
+                precision="fp64", partition="gauss") -> dsnu_params:
+    return dsnu_params(nx=int(nx), ny=int(ny), lx=float(lx), ly=float(ly),
+                       cut_radius=float(cut_radius), sigma=float(sigma), n_r=int(n_r),
+                       n_theta=int(n_theta), kernel_width=int(kernel_width), pad_factor=2,
+                       precision=_PREC[precision], partition=_PART[partition])
+
+
+class Plan:
+    """A solver plan on one CUDA device with a torch-owned workspace.
+
+    ``solve(rho)`` takes a contiguous float64 (ny, nx) CUDA tensor and returns
+    Phi (float64, same shape), enqueued on the current torch stream."""
+
+    def __init__(self, nx, ny=None, lx=None, ly=None, cut_radius=None, n_r=None, n_theta=None,
+                 sigma=0.0, kernel_width=0, precision="fp64", partition="gauss", device=None):
+        import torch
+
+        ny = nx if ny is None else ny
+        ly = lx if ly is None else ly
+        dev = torch.device(device if device is not None else "cuda")
+        if dev.type != "cuda":
+            raise ValueError("the solver runs on CUDA devices only")
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.params = make_params(nx, ny, lx, ly, cut_radius, n_r, n_theta, sigma, kernel_width,
+                                  precision, partition)
+        self.shape = (int(ny), int(nx))
+        self._handle = None
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            self._handle = dsnu_plan_create(self.params, stream)
+            nbytes = dsnu_workspace_bytes(self._handle)
+            self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+            dsnu_set_workspace(self._handle, self.workspace.data_ptr(), self.workspace.numel())
+        self.info = dsnu_plan_get_info(self._handle)
+
+    @property
+    def handle(self) -> int:
+        return self._handle
+
+    def _check_input(self, x):
+        import torch
+
+        if not isinstance(x, torch.Tensor) or x.dtype != torch.float64:
+            raise TypeError("expected a float64 torch tensor")
+        if x.device != self.device:
+            raise ValueError(f"tensor on {x.device}, plan on {self.device}")
+        if tuple(x.shape) != self.shape:
+            raise ValueError(f"expected shape {self.shape}, got {tuple(x.shape)}")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+
+    def _run(self, fn, x, out):
+        import torch
+
+        self._check_input(x)
+        if out is None:
+            out = torch.empty_like(x)
+        else:
+            self._check_input(out)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        fn(self._handle, x.data_ptr(), out.data_ptr(), stream)
+        return out
+
+    def solve(self, rho, out=None):
+        return self._run(dsnu_solve, rho, out)
+
+    def solve_adjoint(self, g, out=None):
+        return self._run(dsnu_solve_adjoint, g, out)
+
+    def status_poll(self) -> int:
+        import torch
+
+        return dsnu_status_poll(self._handle, torch.cuda.current_stream(self.device).cuda_stream)
+
+    def close(self):
+        if self._handle is not None:
+            import torch
+
+            torch.cuda.synchronize(self.device)
+            dsnu_plan_destroy(self._handle)
+            self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

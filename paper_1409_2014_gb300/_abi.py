@@ -1,0 +1,140 @@
+"""ctypes declarations of the C ABI in include/dsnufft.h (argument marshalling
+only; every step of a solve runs in the library's CUDA kernels).
+
+The library is the in-tree ``libdsnufft.so``; there is no fallback: when it is
+missing or fails to load, every entry point raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdsnufft.so")
+
+DSNU_OK, DSNU_EINVAL, DSNU_ENOMEM, DSNU_ECUDA, DSNU_ETIMEOUT, DSNU_EUNSUPPORTED = range(6)
+DSNU_FP64, DSNU_MIXED = 0, 1
+DSNU_PARTITION_GAUSS, DSNU_PARTITION_SHARP = 0, 1
+
+STATUS_NAMES = {0: "DSNU_OK", 1: "DSNU_EINVAL", 2: "DSNU_ENOMEM", 3: "DSNU_ECUDA",
+                4: "DSNU_ETIMEOUT", 5: "DSNU_EUNSUPPORTED"}
+
+EXPORTED = [
+    "dsnu_plan_create", "dsnu_workspace_bytes", "dsnu_set_workspace", "dsnu_solve",
+    "dsnu_solve_adjoint", "dsnu_status_poll", "dsnu_plan_destroy", "dsnu_last_error",
+    "dsnu_plan_get_info",
+]
+
+
+class dsnu_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+        ("cut_radius", ctypes.c_double), ("sigma", ctypes.c_double),
+        ("n_r", ctypes.c_int32), ("n_theta", ctypes.c_int32),
+        ("kernel_width", ctypes.c_int32), ("pad_factor", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("partition", ctypes.c_int32),
+    ]
+
+
+class dsnu_plan_info(ctypes.Structure):
+    _fields_ = [
+        ("n_nodes", ctypes.c_int32), ("band_q", ctypes.c_int32),
+        ("kernel_width", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("sigma", ctypes.c_double), ("es_beta", ctypes.c_double),
+        ("n_tiles", ctypes.c_int32), ("max_tile_nodes", ctypes.c_int32),
+    ]
+
+
+class DsnuError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the library and declare every entry point (raises if missing)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not built: run paper_1409_2014_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp, st = ctypes.c_void_p, ctypes.c_int
+    lib.dsnu_plan_create.argtypes = [ctypes.POINTER(dsnu_params), vp, ctypes.POINTER(vp)]
+    lib.dsnu_plan_create.restype = st
+    lib.dsnu_workspace_bytes.argtypes = [vp]
+    lib.dsnu_workspace_bytes.restype = ctypes.c_size_t
+    lib.dsnu_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.dsnu_set_workspace.restype = st
+    for name in ("dsnu_solve", "dsnu_solve_adjoint"):
+        getattr(lib, name).argtypes = [vp, vp, vp, vp]
+        getattr(lib, name).restype = st
+    lib.dsnu_status_poll.argtypes = [vp, vp]
+    lib.dsnu_status_poll.restype = st
+    lib.dsnu_plan_destroy.argtypes = [vp]
+    lib.dsnu_plan_destroy.restype = st
+    lib.dsnu_last_error.argtypes = []
+    lib.dsnu_last_error.restype = ctypes.c_char_p
+    lib.dsnu_plan_get_info.argtypes = [vp, ctypes.POINTER(dsnu_plan_info)]
+    lib.dsnu_plan_get_info.restype = st
+    _LIB = lib
+    return lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != DSNU_OK:
+        msg = load().dsnu_last_error().decode(errors="replace")
+        raise DsnuError(status, where, msg)
+
+
+# Thin wrappers with the ABI's names ------------------------------------------
+
+def dsnu_plan_create(params: dsnu_params, stream: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(load().dsnu_plan_create(ctypes.byref(params), ctypes.c_void_p(stream), ctypes.byref(out)),
+           "dsnu_plan_create")
+    return out.value
+
+
+def dsnu_workspace_bytes(plan: int) -> int:
+    return int(load().dsnu_workspace_bytes(ctypes.c_void_p(plan)))
+
+
+def dsnu_set_workspace(plan: int, ptr: int, nbytes: int) -> None:
+    _check(load().dsnu_set_workspace(ctypes.c_void_p(plan), ctypes.c_void_p(ptr), nbytes),
+           "dsnu_set_workspace")
+
+
+def dsnu_solve(plan: int, rho_ptr: int, phi_ptr: int, stream: int = 0) -> None:
+    _check(load().dsnu_solve(ctypes.c_void_p(plan), ctypes.c_void_p(rho_ptr),
+                             ctypes.c_void_p(phi_ptr), ctypes.c_void_p(stream)), "dsnu_solve")
+
+
+def dsnu_solve_adjoint(plan: int, g_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    _check(load().dsnu_solve_adjoint(ctypes.c_void_p(plan), ctypes.c_void_p(g_ptr),
+                                     ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream)),
+           "dsnu_solve_adjoint")
+
+
+def dsnu_status_poll(plan: int, stream: int = 0) -> int:
+    return int(load().dsnu_status_poll(ctypes.c_void_p(plan), ctypes.c_void_p(stream)))
+
+
+def dsnu_plan_destroy(plan: int) -> None:
+    _check(load().dsnu_plan_destroy(ctypes.c_void_p(plan)), "dsnu_plan_destroy")
+
+
+def dsnu_last_error() -> str:
+    return load().dsnu_last_error().decode(errors="replace")
+
+
+def dsnu_plan_get_info(plan: int) -> dsnu_plan_info:
+    info = dsnu_plan_info()
+    _check(load().dsnu_plan_get_info(ctypes.c_void_p(plan), ctypes.byref(info)), "dsnu_plan_get_info")
+    return info

@@ -1,0 +1,201 @@
+// common.cuh -- complex type and the in-CTA FFT used by every pipeline kernel.
+//
+// The split solver (Sec. 2.1 of the paper) needs, per grid row or column, a
+// length-M = 2N DFT of data that is non-zero on N points only (the kappa = 2
+// zero padding of I1, which is also the upsampling-2 fine grid of both NUFFTs),
+// or an inverse length-M DFT of which only N outputs are kept.  Both reduce to
+// two length-N DFTs (the even and the odd output frequencies):
+//     Z(2k)   = DFT_N[z](k),     Z(2k+1) = DFT_N[z(n) w_M^n](k),   w_M = e^{-2 pi i/M}
+//     T(n)    = IDFT_N[W(2k)](n) + w_M^{-n} IDFT_N[W(2k+1)](n),      n < N
+// so the only transform primitive is a length-N complex DFT (Sec. 2.2, the
+// uniform DFT pair), done here by a group of N/16 threads of one CTA with the
+// data in shared memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dsnu {
+
+template <typename R>
+struct alignas(2 * sizeof(R)) cpx {
+  R x, y;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> mk(R x, R y) { cpx<R> c; c.x = x; c.y = y; return c; }
+template <typename R>
+__device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
+template <typename R>
+__device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+template <typename R>
+__device__ __forceinline__ cpx<R> operator*(cpx<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
+template <typename R>
+__device__ __forceinline__ cpx<R> cmul(cpx<R> a, cpx<R> b) {
+  return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename R>
+__device__ __forceinline__ cpx<R> cmulc(cpx<R> a, cpx<R> b) {
+  return mk<R>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> conj(cpx<R> a) { return mk<R>(a.x, -a.y); }
+// multiply by +i (s = +1) or -i (s = -1)
+template <typename R>
+__device__ __forceinline__ cpx<R> mul_i(cpx<R> a, int s) { return s > 0 ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x); }
+// multiply by i^e, e taken mod 4
+template <typename R>
+__device__ __forceinline__ cpx<R> mul_ipow(cpx<R> a, int e) {
+  switch (e & 3) {
+    case 0: return a;
+    case 1: return mk<R>(-a.y, a.x);
+    case 2: return mk<R>(-a.x, -a.y);
+    default: return mk<R>(a.y, -a.x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small forward DFTs in registers (e^{-2 pi i jk/RAD}), RAD = 2, 4, 8, 16,
+// by radix-2 decimation in time with the constant twiddles of the 16th roots
+// of unity written out: cos(pi/8) = sqrt(2+sqrt 2)/2, sin(pi/8) =
+// sqrt(2-sqrt 2)/2, cos(pi/4) = sqrt(1/2).
+// ---------------------------------------------------------------------------
+constexpr double kC1_16 = 0.92387953251128675613;  // cos(2 pi/16)
+constexpr double kS1_16 = 0.38268343236508977173;  // sin(2 pi/16)
+constexpr double kR2 = 0.70710678118654752440;     // sqrt(1/2)
+
+// x * e^{-2 pi i m/16}, m in [0, 8)
+template <int M16, typename R>
+__device__ __forceinline__ cpx<R> rot16(cpx<R> a) {
+  if constexpr (M16 == 0) {
+    return a;
+  } else if constexpr (M16 == 4) {          // -i
+    return mk<R>(a.y, -a.x);
+  } else if constexpr (M16 == 2) {          // (1 - i)/sqrt2
+    return mk<R>(R(kR2) * (a.x + a.y), R(kR2) * (a.y - a.x));
+  } else if constexpr (M16 == 6) {          // (-1 - i)/sqrt2
+    return mk<R>(R(kR2) * (a.y - a.x), R(-kR2) * (a.x + a.y));
+  } else {
+    // cos/sin of 2 pi m/16 for m = 1, 3, 5, 7
+    constexpr double c = (M16 == 1) ? kC1_16 : (M16 == 3) ? kS1_16 : (M16 == 5) ? -kS1_16 : -kC1_16;
+    constexpr double s = (M16 == 1) ? kS1_16 : (M16 == 3) ? kC1_16 : (M16 == 5) ? kC1_16 : kS1_16;
+    // (x + i y)(c - i s)
+    return mk<R>(a.x * R(c) + a.y * R(s), a.y * R(c) - a.x * R(s));
+  }
+}
+
+// In-place forward DFT of v[0..RAD) (natural order in and out).
+template <int RAD, typename R>
+__device__ __forceinline__ void dft_rec(cpx<R> (&v)[RAD]) {
+  if constexpr (RAD == 1) {
+    return;
+  } else if constexpr (RAD == 2) {
+    cpx<R> a = v[0], b = v[1];
+    v[0] = a + b;
+    v[1] = a - b;
+  } else {
+    constexpr int H = RAD / 2;
+    cpx<R> e[H], o[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
+    dft_rec<H, R>(e);
+    dft_rec<H, R>(o);
+    constexpr int step = 16 / RAD;
+    // twiddle o[k] by e^{-2 pi i k/RAD} = rot16<k*step>
+#define DSNU_TW(K)                                                         \
+  if constexpr ((K) < H) {                                                 \
+    cpx<R> t = rot16<((K) * step) & 15, R>(o[(K)]);                        \
+    v[(K)] = e[(K)] + t;                                                   \
+    v[(K) + H] = e[(K)] - t;                                               \
+  }
+    DSNU_TW(0) DSNU_TW(1) DSNU_TW(2) DSNU_TW(3) DSNU_TW(4) DSNU_TW(5) DSNU_TW(6) DSNU_TW(7)
+#undef DSNU_TW
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Length-N forward DFT (e^{-2 pi i nk/N}) of buf[0..N) in shared memory by the
+// G = N/16 threads t = 0..G-1 of one group; every thread of the CTA must call
+// it (it contains __syncthreads).  Stockham autosort, radix-16 stages then one
+// radix-2/4/8 stage; natural order in and out.  `tw` = e^{-2 pi i m/N}, m < N,
+// generated in FP64 on the host.  With inv = true the DFT is the inverse
+// (e^{+2 pi i nk/N}, unnormalised), computed as conj(DFT(conj x)) with the
+// conjugations folded into the first loads and the last stores.
+// The caller synchronises before the call (inputs written); the call ends
+// with a barrier (outputs visible).
+// ---------------------------------------------------------------------------
+template <int LOG2N, int S>
+struct StageInfo {
+  static constexpr int full = LOG2N / 4;
+  static constexpr int lr = (S < full) ? 4 : (LOG2N - 4 * full);
+  static constexpr int nstages = (LOG2N + 3) / 4;
+};
+
+template <typename R, int LOG2N, int LR, int LOG2NS, bool FIRST, bool LAST>
+__device__ __forceinline__ void fft_stage(cpx<R>* buf, int t, bool active,
+                                          const cpx<R>* __restrict__ tw, bool inv) {
+  constexpr int N = 1 << LOG2N;
+  constexpr int RAD = 1 << LR;
+  constexpr int NB = N / RAD;
+  constexpr int G = N / 16;
+  constexpr int PER = 16 / RAD;
+  constexpr int NS = 1 << LOG2NS;
+  cpx<R> v[PER][RAD];
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+      const int j = t + b * G;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) {
+        cpx<R> a = buf[j + r * NB];
+        if (FIRST && inv) a.y = -a.y;
+        v[b][r] = a;
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+      const int j = t + b * G;
+      const int k = j & (NS - 1);
+      if constexpr (LOG2NS > 0) {
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) {
+          const int m = (r * k) << (LOG2N - LOG2NS - LR);
+          v[b][r] = cmul(v[b][r], tw[m]);
+        }
+      }
+      dft_rec<RAD, R>(v[b]);
+      const int base = (j - k) * RAD + k;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) {
+        cpx<R> a = v[b][r];
+        if (LAST && inv) a.y = -a.y;
+        buf[base + r * NS] = a;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename R, int LOG2N, int S, int LOG2NS>
+__device__ __forceinline__ void fft_stages(cpx<R>* buf, int t, bool active,
+                                           const cpx<R>* __restrict__ tw, bool inv) {
+  using SI = StageInfo<LOG2N, S>;
+  if constexpr (S < SI::nstages) {
+    constexpr int LR = SI::lr;
+    fft_stage<R, LOG2N, LR, LOG2NS, S == 0, S == SI::nstages - 1>(buf, t, active, tw, inv);
+    fft_stages<R, LOG2N, S + 1, LOG2NS + LR>(buf, t, active, tw, inv);
+  }
+}
+
+template <typename R, int LOG2N>
+__device__ __forceinline__ void block_fft(cpx<R>* buf, int t, bool active,
+                                          const cpx<R>* __restrict__ tw, bool inv) {
+  static_assert(LOG2N >= 4 && LOG2N <= 13, "FFT length 16..8192");
+  fft_stages<R, LOG2N, 0, 0>(buf, t, active, tw, inv);
+}
+
+}  // namespace dsnu

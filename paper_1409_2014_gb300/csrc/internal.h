@@ -1,0 +1,70 @@
+// internal.h -- plan layout shared by the host plan builder and the launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "dsnufft.h"
+
+namespace dsnu {
+
+// Device tables of a plan.  Real-valued tables are in the plan's working
+// precision (float for DSNU_MIXED, double for DSNU_FP64); node_D is FP64.
+struct PlanTables {
+  void* twN_x;    // cpx, nx   e^{-2 pi i m/nx}
+  void* twM_x;    // cpx, nx   e^{-2 pi i n/Mx}
+  void* decon_x;  // real, nx  phi_hat(0)/phi_hat(2 pi (n - nx/2)/Mx)
+  void* twN_y;
+  void* twM_y;
+  void* decon_y;
+  void* m_wx2;    // real, nx + 1
+  void* m_gx;     // real, nx + 1
+  void* m_wy2;    // real, My
+  void* m_gy;     // real, My
+  int2* node_q0;  // n_nodes
+  void* node_w;   // real, n_nodes * 2w (x weights then y weights)
+  double* node_D; // n_nodes
+  int* tile_ptr;  // n_tiles + 1
+  int* tile_nodes;
+  int* status;    // one int
+};
+
+// Workspace layout (offsets in bytes from the workspace base).
+struct WsLayout {
+  size_t off_A, off_B, off_Bband, off_Sband, off_c, total;
+  int lda, ldb, ldq;
+};
+
+struct PlanGeom {
+  int nx, ny, mx, my, log2nx, log2ny;
+  int w, Q, n_nodes, n_tiles, tiles_x, tiles_y, max_tile_nodes;
+  int precision, sharp;
+  double beta, sigma, cut_radius;
+  double scale;  // 1/(Mx My)
+};
+
+// Launchers (one translation unit per precision).
+dsnu_status run_pipeline_f32(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
+                             const double* rho, double* phi, cudaStream_t st, int cj);
+dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
+                             const double* rho, double* phi, cudaStream_t st, int cj);
+cudaError_t prepare_kernels_f32(int log2nx, int log2ny);
+cudaError_t prepare_kernels_f64(int log2nx, int log2ny);
+
+void set_last_error(const std::string& msg);
+
+}  // namespace dsnu
+
+struct dsnu_plan_s {
+  dsnu_params prm;          // resolved parameters
+  dsnu::PlanGeom geom;
+  dsnu::PlanTables tab;
+  dsnu::WsLayout ws_layout;
+  void* table_block;        // one device allocation holding every table
+  size_t table_bytes;
+  void* ws;                 // caller-owned workspace
+  size_t ws_bytes;
+};

@@ -1,0 +1,440 @@
+// plan.cu -- host side: parameter checks, FP64 plan tables, the C ABI.
+//
+// Plan tables (Sec. 2.1 of the paper, all generated in FP64 here):
+//   * radial Gauss-Legendre nodes/weights on [0, P] (Newton iteration on the
+//     Legendre three-term recurrence) and the uniform angular rule
+//     theta_j = 2 pi j / N_theta  -> polar nodes k_ij = r_i (cos, sin) theta_j;
+//   * weights D_ij = -(2 pi)^-2 r_i w_i (2 pi/N_theta) cos^2(theta_j) p(r_i)
+//     (eq. I2PolarDisc with the Jacobian r and the angular-frequency
+//     normalisation written in);
+//   * the exponential-of-semicircle (ES) kernel phi(z) = exp(beta (sqrt(1 -
+//     (2z/w)^2) - 1)) on |z| <= w/2 fine-grid cells, beta = 2.30 w (Barnett,
+//     Magland, af Klinteberg 2019, upsampling 2), its per-node separable
+//     weights and its Fourier transform phi_hat (deconvolution);
+//   * twiddles e^{-2 pi i m/N} and e^{-2 pi i n/M}, and the axis tables of the
+//     high-frequency multiplier (1 - p) (-k_x^2/|k|^2);
+//   * the spreading tiles' node lists (nodes are fixed per plan).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace dsnu {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+static dsnu_status fail(dsnu_status st, const std::string& msg) {
+  set_last_error(msg);
+  return st;
+}
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+static int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+// Gauss-Legendre nodes (ascending) and weights on [-1, 1].
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = (n == 1) ? 1.0 : n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = (n == 1) ? 1.0 : n * (z * p1 - p0) / (z * z - 1.0);
+    }
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+static double es_kernel(double z, int w, double beta) {
+  const double t = 2.0 * z / w;
+  const double u = 1.0 - t * t;
+  if (u < 0.0) return 0.0;
+  return std::exp(beta * (std::sqrt(u) - 1.0));
+}
+
+// phi_hat(xi) = int_{-w/2}^{w/2} phi(z) e^{-i xi z} dz, by Gauss-Legendre in
+// t with z = (w/2) sin t (smooth integrand on [0, pi/2]).
+struct EsFourier {
+  std::vector<double> t, v;
+  int w;
+  double beta;
+  EsFourier(int w_, double beta_) : w(w_), beta(beta_) {
+    std::vector<double> x, ww;
+    gauss_legendre(200, x, ww);
+    t.resize(x.size());
+    v.resize(x.size());
+    for (size_t i = 0; i < x.size(); ++i) {
+      t[i] = (x[i] + 1.0) * M_PI / 4.0;
+      v[i] = ww[i] * M_PI / 4.0;
+    }
+  }
+  double operator()(double xi) const {
+    const double hw = 0.5 * w;
+    double s = 0.0;
+    for (size_t i = 0; i < t.size(); ++i) {
+      const double z = hw * std::sin(t[i]);
+      s += v[i] * std::exp(beta * (std::cos(t[i]) - 1.0)) * hw * std::cos(t[i]) * std::cos(xi * z);
+    }
+    return 2.0 * s;
+  }
+};
+
+template <typename R>
+struct HostTables {
+  std::vector<R> twN_x, twM_x, decon_x, twN_y, twM_y, decon_y;  // twiddles interleaved re, im
+  std::vector<R> m_wx2, m_gx, m_wy2, m_gy;
+  std::vector<int2> node_q0;
+  std::vector<R> node_w;
+  std::vector<double> node_D;
+  std::vector<int> tile_ptr, tile_nodes;
+};
+
+static void twiddles(int n, int m, std::vector<double>& out) {
+  out.resize(2 * n);
+  for (int i = 0; i < n; ++i) {
+    const double a = -2.0 * M_PI * double(i) / double(m);
+    out[2 * i] = std::cos(a);
+    out[2 * i + 1] = std::sin(a);
+  }
+}
+
+template <typename R>
+static std::vector<R> cast(const std::vector<double>& v) {
+  return std::vector<R>(v.begin(), v.end());
+}
+
+struct Builder {
+  std::vector<unsigned char> bytes;
+  size_t add(const void* p, size_t n) {
+    const size_t off = (bytes.size() + 255) & ~size_t(255);
+    bytes.resize(off + n);
+    if (n) std::memcpy(bytes.data() + off, p, n);
+    return off;
+  }
+  template <typename T>
+  size_t add(const std::vector<T>& v) { return add(v.data(), v.size() * sizeof(T)); }
+};
+
+template <typename R>
+static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
+  const dsnu_params& p = P->prm;
+  PlanGeom& g = P->geom;
+  const int nx = g.nx, ny = g.ny, Mx = g.mx, My = g.my, w = g.w;
+  const double hx = 2.0 * p.lx / nx, hy = 2.0 * p.ly / ny;
+  const double dkx = 2.0 * M_PI / (Mx * hx), dky = 2.0 * M_PI / (My * hy);
+  const double sigma = g.sigma, beta = g.beta;
+
+  // polar nodes and weights
+  std::vector<double> gx, gw;
+  gauss_legendre(p.n_r, gx, gw);
+  const int nn = p.n_r * p.n_theta;
+  std::vector<double> kx(nn), ky(nn), D(nn);
+  for (int i = 0; i < p.n_r; ++i) {
+    const double r = 0.5 * p.cut_radius * (gx[i] + 1.0);
+    const double wr = 0.5 * p.cut_radius * gw[i];
+    const double pr = g.sharp ? 1.0 : std::exp(-r * r / (sigma * sigma));
+    for (int j = 0; j < p.n_theta; ++j) {
+      const double th = 2.0 * M_PI * j / p.n_theta;
+      const double c = std::cos(th), s = std::sin(th);
+      kx[i * p.n_theta + j] = r * c;
+      ky[i * p.n_theta + j] = r * s;
+      D[i * p.n_theta + j] = -(r * wr * (2.0 * M_PI / p.n_theta) * c * c * pr) / (4.0 * M_PI * M_PI);
+    }
+  }
+
+  // ES kernel tables
+  EsFourier fh(w, beta);
+  const double ph0 = fh(0.0);
+  HostTables<R> T;
+  std::vector<double> tmp;
+  twiddles(nx, nx, tmp); T.twN_x = cast<R>(tmp);
+  twiddles(nx, Mx, tmp); T.twM_x = cast<R>(tmp);
+  twiddles(ny, ny, tmp); T.twN_y = cast<R>(tmp);
+  twiddles(ny, My, tmp); T.twM_y = cast<R>(tmp);
+  T.decon_x.resize(nx);
+  for (int n = 0; n < nx; ++n) T.decon_x[n] = R(ph0 / fh(2.0 * M_PI * (n - nx / 2) / Mx));
+  T.decon_y.resize(ny);
+  for (int n = 0; n < ny; ++n) T.decon_y[n] = R(ph0 / fh(2.0 * M_PI * (n - ny / 2) / My));
+
+  // multiplier axis tables
+  T.m_wx2.resize(nx + 1);
+  T.m_gx.resize(nx + 1);
+  for (int q = 0; q <= nx; ++q) {
+    const double a = q * dkx;
+    T.m_wx2[q] = R(a * a);
+    T.m_gx[q] = R(-std::expm1(-(a * a) / (sigma * sigma)));
+  }
+  T.m_wy2.resize(My);
+  T.m_gy.resize(My);
+  for (int q = 0; q < My; ++q) {
+    const int qs = q < ny ? q : q - My;
+    const double a = qs * dky;
+    T.m_wy2[q] = R(a * a);
+    T.m_gy[q] = R(-std::expm1(-(a * a) / (sigma * sigma)));
+  }
+
+  // per-node stencils
+  T.node_q0.resize(nn);
+  T.node_w.resize(size_t(nn) * 2 * w);
+  T.node_D.resize(nn);
+  int Q = 0;
+  for (int j = 0; j < nn; ++j) {
+    const double ux = kx[j] / dkx, uy = ky[j] / dky;
+    const int q0x = int(std::ceil(ux - 0.5 * w));
+    const int q0y = int(std::ceil(uy - 0.5 * w));
+    T.node_q0[j] = make_int2(q0x, q0y);
+    for (int a = 0; a < w; ++a) {
+      T.node_w[size_t(j) * 2 * w + a] = R(es_kernel(ux - (q0x + a), w, beta));
+      T.node_w[size_t(j) * 2 * w + w + a] = R(es_kernel(uy - (q0y + a), w, beta));
+    }
+    Q = std::max({Q, std::abs(q0x), std::abs(q0x + w - 1), std::abs(q0y), std::abs(q0y + w - 1)});
+    // rho_hat = hx hy / phi_hat(0)^2 * (stencil sum), then the type-1 scale
+    // Mx My / phi_hat(0)^2 so that both halves of the final complex inverse
+    // transform carry comparable magnitudes.
+    T.node_D[j] = D[j] * (hx * hy / (ph0 * ph0)) * (double(Mx) * double(My) / (ph0 * ph0));
+  }
+  if (Q > nx - 1 || Q > ny - 1)
+    return fail(DSNU_EINVAL, "disk plus ES stencil does not fit the padded grid: need P*h + w*pi/M < pi");
+  g.Q = Q;
+
+  // spreading tiles over q_x in [0, Q], q_y in [-Q, Q]
+  g.tiles_x = (Q + 1 + 15) / 16;
+  g.tiles_y = (2 * Q + 1 + 15) / 16;
+  g.n_tiles = g.tiles_x * g.tiles_y;
+  std::vector<std::vector<int>> lists(g.n_tiles);
+  for (int j = 0; j < nn; ++j) {
+    const int xlo = std::max(T.node_q0[j].x, 0), xhi = std::min(T.node_q0[j].x + w - 1, Q);
+    if (xhi < xlo) continue;
+    const int ylo = T.node_q0[j].y + Q, yhi = T.node_q0[j].y + w - 1 + Q;
+    for (int ty = ylo / 16; ty <= yhi / 16; ++ty)
+      for (int tx = xlo / 16; tx <= xhi / 16; ++tx) lists[ty * g.tiles_x + tx].push_back(j);
+  }
+  T.tile_ptr.assign(g.n_tiles + 1, 0);
+  g.max_tile_nodes = 0;
+  for (int i = 0; i < g.n_tiles; ++i) {
+    T.tile_ptr[i + 1] = T.tile_ptr[i] + int(lists[i].size());
+    g.max_tile_nodes = std::max(g.max_tile_nodes, int(lists[i].size()));
+  }
+  T.tile_nodes.reserve(T.tile_ptr.back() + 1);
+  for (auto& l : lists) T.tile_nodes.insert(T.tile_nodes.end(), l.begin(), l.end());
+  if (T.tile_nodes.empty()) T.tile_nodes.push_back(0);
+
+  // one device block for every table
+  Builder b;
+  const size_t o_twNx = b.add(T.twN_x), o_twMx = b.add(T.twM_x), o_dx = b.add(T.decon_x);
+  const size_t o_twNy = b.add(T.twN_y), o_twMy = b.add(T.twM_y), o_dy = b.add(T.decon_y);
+  const size_t o_wx2 = b.add(T.m_wx2), o_gx = b.add(T.m_gx), o_wy2 = b.add(T.m_wy2), o_gy = b.add(T.m_gy);
+  const size_t o_q0 = b.add(T.node_q0), o_w = b.add(T.node_w), o_D = b.add(T.node_D);
+  const size_t o_tp = b.add(T.tile_ptr), o_tn = b.add(T.tile_nodes);
+  const int zero = 0;
+  const size_t o_st = b.add(&zero, sizeof(int));
+  void* dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, b.bytes.size());
+  if (e != cudaSuccess) return fail(DSNU_ENOMEM, std::string("cudaMalloc(plan tables): ") + cudaGetErrorString(e));
+  e = cudaMemcpyAsync(dev, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    return fail(DSNU_ECUDA, std::string("plan table upload: ") + cudaGetErrorString(e));
+  }
+  char* d = static_cast<char*>(dev);
+  PlanTables& t = P->tab;
+  t.twN_x = d + o_twNx; t.twM_x = d + o_twMx; t.decon_x = d + o_dx;
+  t.twN_y = d + o_twNy; t.twM_y = d + o_twMy; t.decon_y = d + o_dy;
+  t.m_wx2 = d + o_wx2; t.m_gx = d + o_gx; t.m_wy2 = d + o_wy2; t.m_gy = d + o_gy;
+  t.node_q0 = reinterpret_cast<int2*>(d + o_q0);
+  t.node_w = d + o_w;
+  t.node_D = reinterpret_cast<double*>(d + o_D);
+  t.tile_ptr = reinterpret_cast<int*>(d + o_tp);
+  t.tile_nodes = reinterpret_cast<int*>(d + o_tn);
+  t.status = reinterpret_cast<int*>(d + o_st);
+  P->table_block = dev;
+  P->table_bytes = b.bytes.size();
+  return DSNU_OK;
+}
+
+static void layout_workspace(dsnu_plan_s* P) {
+  const PlanGeom& g = P->geom;
+  const size_t csz = (g.precision == DSNU_MIXED) ? 8 : 16;
+  WsLayout& L = P->ws_layout;
+  L.lda = g.nx + 2;
+  L.ldb = (g.Q + 2) & ~1;
+  L.ldq = 2 * g.Q + 1;
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    const size_t o = off;
+    off = (off + n + 255) & ~size_t(255);
+    return o;
+  };
+  L.off_A = take(size_t(g.ny) * L.lda * csz);
+  L.off_B = take(size_t(g.ny) * L.ldb * csz);
+  L.off_Bband = take(size_t(g.Q + 1) * L.ldq * csz);
+  L.off_Sband = take(size_t(g.Q + 1) * L.ldq * csz);
+  L.off_c = take(size_t(g.n_nodes) * csz);
+  L.total = off;
+}
+
+}  // namespace dsnu
+
+using namespace dsnu;
+
+extern "C" {
+
+const char* dsnu_last_error(void) { return g_last_error.c_str(); }
+
+dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan* out) {
+  if (!params || !out) return fail(DSNU_EINVAL, "NULL params or out");
+  dsnu_params p = *params;
+  if (!is_pow2(p.nx) || !is_pow2(p.ny) || p.nx < 16 || p.ny < 16 || p.nx > 4096 || p.ny > 4096)
+    return fail(DSNU_EINVAL, "nx, ny must be powers of two in [16, 4096]");
+  if (!(p.lx > 0.0) || !(p.ly > 0.0) || !std::isfinite(p.lx) || !std::isfinite(p.ly))
+    return fail(DSNU_EINVAL, "lx, ly must be positive and finite");
+  if (!(p.cut_radius > 0.0) || !std::isfinite(p.cut_radius)) return fail(DSNU_EINVAL, "cut_radius must be positive");
+  if (p.sigma < 0.0 || !std::isfinite(p.sigma)) return fail(DSNU_EINVAL, "sigma must be >= 0");
+  if (p.n_r < 1 || p.n_r > 4096) return fail(DSNU_EINVAL, "n_r must be in [1, 4096]");
+  if (p.n_theta < 2 || (p.n_theta & 1) || p.n_theta > 65536) return fail(DSNU_EINVAL, "n_theta must be even, >= 2");
+  if (p.precision != DSNU_FP64 && p.precision != DSNU_MIXED) return fail(DSNU_EINVAL, "unknown precision");
+  if (p.partition != DSNU_PARTITION_GAUSS && p.partition != DSNU_PARTITION_SHARP)
+    return fail(DSNU_EINVAL, "unknown partition");
+  if (p.pad_factor != 0 && p.pad_factor != 2) return fail(DSNU_EUNSUPPORTED, "only pad_factor = 2 is supported");
+  if (p.kernel_width == 0) p.kernel_width = (p.precision == DSNU_FP64) ? 15 : 8;
+  if (p.kernel_width < 2 || p.kernel_width > 16) return fail(DSNU_EINVAL, "kernel_width must be in [2, 16]");
+  if (p.sigma == 0.0) p.sigma = p.cut_radius / 6.0;
+  p.pad_factor = 2;
+  if (long(p.n_r) * long(p.n_theta) > (1L << 24)) return fail(DSNU_EINVAL, "too many polar nodes");
+
+  dsnu_plan_s* P = new (std::nothrow) dsnu_plan_s();
+  if (!P) return fail(DSNU_ENOMEM, "host allocation failed");
+  P->prm = p;
+  PlanGeom& g = P->geom;
+  g.nx = p.nx;
+  g.ny = p.ny;
+  g.mx = 2 * p.nx;
+  g.my = 2 * p.ny;
+  g.log2nx = ilog2(p.nx);
+  g.log2ny = ilog2(p.ny);
+  g.w = p.kernel_width;
+  g.beta = 2.30 * p.kernel_width;
+  g.sigma = p.sigma;
+  g.cut_radius = p.cut_radius;
+  g.n_nodes = p.n_r * p.n_theta;
+  g.precision = p.precision;
+  g.sharp = (p.partition == DSNU_PARTITION_SHARP);
+  g.scale = 1.0 / (double(g.mx) * double(g.my));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  dsnu_status s = (p.precision == DSNU_MIXED) ? build_tables<float>(P, st) : build_tables<double>(P, st);
+  if (s != DSNU_OK) {
+    delete P;
+    return s;
+  }
+  const cudaError_t e = (p.precision == DSNU_MIXED) ? prepare_kernels_f32(g.log2nx, g.log2ny)
+                                                    : prepare_kernels_f64(g.log2nx, g.log2ny);
+  if (e != cudaSuccess) {
+    cudaFree(P->table_block);
+    delete P;
+    return fail(DSNU_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+  }
+  layout_workspace(P);
+  *out = P;
+  return DSNU_OK;
+}
+
+size_t dsnu_workspace_bytes(dsnu_plan plan) { return plan ? plan->ws_layout.total : 0; }
+
+dsnu_status dsnu_set_workspace(dsnu_plan plan, void* ws, size_t bytes) {
+  if (!plan || !ws) return fail(DSNU_EINVAL, "NULL plan or workspace");
+  if (bytes < plan->ws_layout.total) return fail(DSNU_EINVAL, "workspace too small");
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(DSNU_EINVAL, "workspace must be 256-byte aligned");
+  plan->ws = ws;
+  plan->ws_bytes = bytes;
+  return DSNU_OK;
+}
+
+static dsnu_status run(dsnu_plan plan, const double* in, double* out, void* stream, int cj) {
+  if (!plan) return fail(DSNU_EINVAL, "NULL plan");
+  if (!in || !out) return fail(DSNU_EINVAL, "NULL input or output");
+  if (!plan->ws) return fail(DSNU_EINVAL, "no workspace attached (dsnu_set_workspace)");
+  const size_t nbytes = size_t(plan->geom.nx) * plan->geom.ny * sizeof(double);
+  const char* a = reinterpret_cast<const char*>(in);
+  const char* b = reinterpret_cast<const char*>(out);
+  if (a < b + nbytes && b < a + nbytes) return fail(DSNU_EINVAL, "input and output overlap");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (plan->geom.precision == DSNU_MIXED)
+    return run_pipeline_f32(plan->geom, plan->tab, plan->ws_layout, plan->ws, in, out, st, cj);
+  return run_pipeline_f64(plan->geom, plan->tab, plan->ws_layout, plan->ws, in, out, st, cj);
+}
+
+dsnu_status dsnu_solve(dsnu_plan plan, const double* rho, double* phi, void* stream) {
+  return run(plan, rho, phi, stream, 0);
+}
+
+dsnu_status dsnu_solve_adjoint(dsnu_plan plan, const double* g, double* out, void* stream) {
+  return run(plan, g, out, stream, 1);
+}
+
+dsnu_status dsnu_status_poll(dsnu_plan plan, void* stream) {
+  if (!plan) return fail(DSNU_EINVAL, "NULL plan");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, plan->tab.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && h != 0) e = cudaMemsetAsync(plan->tab.status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return fail(DSNU_ECUDA, std::string("status poll: ") + cudaGetErrorString(e));
+  return static_cast<dsnu_status>(h);
+}
+
+dsnu_status dsnu_plan_destroy(dsnu_plan plan) {
+  if (!plan) return DSNU_OK;
+  cudaError_t e = cudaFree(plan->table_block);
+  delete plan;
+  if (e != cudaSuccess) return fail(DSNU_ECUDA, std::string("cudaFree: ") + cudaGetErrorString(e));
+  return DSNU_OK;
+}
+
+dsnu_status dsnu_plan_get_info(dsnu_plan plan, dsnu_plan_info* info) {
+  if (!plan || !info) return fail(DSNU_EINVAL, "NULL plan or info");
+  const PlanGeom& g = plan->geom;
+  info->n_nodes = g.n_nodes;
+  info->band_q = g.Q;
+  info->kernel_width = g.w;
+  info->precision = g.precision;
+  info->sigma = g.sigma;
+  info->es_beta = g.beta;
+  info->n_tiles = g.n_tiles;
+  info->max_tile_nodes = g.max_tile_nodes;
+  return DSNU_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+FP64 plans must match the oracle to relative L-infinity <= 1e-12; mixed plans
+(FP32 FFT butterflies and ES weights) to <= 1e-6.  Inputs are seeded
+synthetic densities (synth/).  Sizes span several CTAs and partial CTAs (rows
+per CTA = 4096 / nx) and the band edge cases.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_2014_gb300.build import build
+
+    build()
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def gpu_solve(rho, prec, adjoint=False, **kw):
+    from paper_1409_2014_gb300 import Plan
+
+    ny, nx = rho.shape
+    plan = Plan(nx, ny, precision=prec, device="cuda:0", **kw)
+    x = torch.from_numpy(np.ascontiguousarray(rho)).to("cuda:0")
+    out = plan.solve_adjoint(x) if adjoint else plan.solve(x)
+    res = out.cpu().numpy()
+    plan.close()
+    return res
+
+
+TOL = {"fp64": 1e-12, "mixed": 1e-6}
+
+CASES = [
+    # nx, ny, lx, ly, P, n_r, n_theta, sigma
+    (16, 16, 4.0, 4.0, 2.0, 8, 16, 0.0),          # brute-force size
+    (32, 32, 8.0, 8.0, 3.0, 12, 24, 0.5),
+    (64, 64, 8.0, 8.0, 4.0, 24, 48, 2 / 3),
+    (64, 32, 8.0, 4.0, 4.0, 24, 48, 2 / 3),       # rectangular, hx == hy
+    (128, 64, 16.0, 4.0, 3.0, 24, 48, 0.5),       # rectangular, hx != hy
+    (128, 128, 16.0, 16.0, 4.0, 32, 64, 2 / 3),   # config 1
+    (256, 256, 16.0, 16.0, 6.0, 32, 64, 1.0),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", CASES)
+def test_small_grids_vs_oracle(case, prec):
+    nx, ny, lx, ly, P, nr, nt, sg = case
+    rho = synth.density_abs2(nx, ny, lx, ly, seed=nx + ny, count=6)
+    op = oracle.OracleParams(nx=nx, ny=ny, lx=lx, ly=ly, cut_radius=P, n_r=nr, n_theta=nt, sigma=sg)
+    ref = oracle.solve(rho, op)
+    got = gpu_solve(rho, prec, lx=lx, ly=ly, cut_radius=P, n_r=nr, n_theta=nt, sigma=sg)
+    assert rel_linf(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_config1_closed_form(prec):
+    """128^2 on [-16,16)^2, rho = exp(-r^2), P = 4, 32 x 64 nodes."""
+    n, L = 128, 16.0
+    rho = synth.isotropic_gaussian(n, n, L, L)
+    op = oracle.OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=4.0, n_r=32, n_theta=64, sigma=2 / 3)
+    ref = oracle.solve(rho, op)
+    got = gpu_solve(rho, prec, lx=L, cut_radius=4.0, n_r=32, n_theta=64, sigma=2 / 3)
+    assert rel_linf(got, ref) <= TOL[prec]
+    x = oracle.grid_axis(n, L)
+    X, Y = np.meshgrid(x, x)
+    assert rel_linf(got, oracle.gaussian_potential(X, Y)) < 1e-6
+
+
+def test_config1_resolved_closed_form_fp64():
+    n, L = 128, 16.0
+    rho = synth.isotropic_gaussian(n, n, L, L)
+    got = gpu_solve(rho, "fp64", lx=L, cut_radius=4.0, n_r=48, n_theta=96, sigma=2 / 3)
+    x = oracle.grid_axis(n, L)
+    X, Y = np.meshgrid(x, x)
+    assert rel_linf(got, oracle.gaussian_potential(X, Y)) < 1e-13
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sharp_partition(prec):
+    n, L = 64, 8.0
+    rho = synth.density_sum(n, n, L, L, seed=9, count=3)
+    op = oracle.OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=3.0, n_r=24, n_theta=48,
+                             partition="sharp")
+    ref = oracle.solve(rho, op)
+    got = gpu_solve(rho, prec, lx=L, cut_radius=3.0, n_r=24, n_theta=48, partition="sharp")
+    assert rel_linf(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_adjoint_vs_oracle_and_symmetry(prec):
+    n, L = 64, 8.0
+    g = np.random.Generator(np.random.PCG64(21))
+    rho = g.standard_normal((n, n))
+    w = g.standard_normal((n, n))
+    kw = dict(lx=L, cut_radius=4.0, n_r=24, n_theta=48, sigma=2 / 3)
+    op = oracle.OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=4.0, n_r=24, n_theta=48, sigma=2 / 3)
+    ref_t = oracle.solve_adjoint(w, op)
+    got_t = gpu_solve(w, prec, adjoint=True, **kw)
+    assert rel_linf(got_t, ref_t) <= TOL[prec]
+    a_rho = gpu_solve(rho, prec, **kw)
+    lhs = float(np.sum(w * a_rho))
+    rhs = float(np.sum(got_t * rho))
+    scale = float(np.abs(w).sum() * np.abs(a_rho).max())
+    assert abs(lhs - rhs) <= 10 * TOL[prec] * scale
+
+
+def test_zero_density_gives_zero():
+    n = 64
+    got = gpu_solve(np.zeros((n, n)), "fp64", lx=8.0, cut_radius=4.0, n_r=24, n_theta=48)
+    assert np.all(got == 0.0)
+
+
+def test_linearity_fp64():
+    n, L = 64, 8.0
+    g = np.random.Generator(np.random.PCG64(5))
+    a, b = g.standard_normal((2, n, n))
+    kw = dict(lx=L, cut_radius=4.0, n_r=24, n_theta=48)
+    lhs = gpu_solve(2.0 * a - 3.0 * b, "fp64", **kw)
+    rhs = 2.0 * gpu_solve(a, "fp64", **kw) - 3.0 * gpu_solve(b, "fp64", **kw)
+    assert np.abs(lhs - rhs).max() <= 1e-13 * np.abs(rhs).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_config2_1024(prec):
+    """1024^2 on [-32,32)^2, 8 seeded anisotropic Gaussians, P = 8, 64 x 256."""
+    n, L = 1024, 32.0
+    rho = synth.density_sum(n, n, L, L, seed=2, count=8)
+    op = oracle.OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=8.0, n_r=64, n_theta=256)
+    rows = np.arange(0, n, 4)
+    cols = np.arange(1, n, 4)
+    ref = oracle.solve(rho, op, rows=rows, cols=cols)
+    got = gpu_solve(rho, prec, lx=L, cut_radius=8.0, n_r=64, n_theta=256)
+    assert rel_linf(got[np.ix_(rows, cols)], ref) <= TOL[prec]
+
+
+def test_repeat_calls_bitwise_identical():
+    from paper_1409_2014_gb300 import Plan
+
+    n = 256
+    rho = torch.from_numpy(synth.density_sum(n, n, 16.0, 16.0, seed=4, count=5)).cuda()
+    plan = Plan(n, lx=16.0, cut_radius=6.0, n_r=32, n_theta=64, precision="mixed")
+    a = plan.solve(rho).clone()
+    b = plan.solve(rho)
+    assert torch.equal(a, b)
+    plan.close()
