@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark: potential solves/s of the split nonlocal potential solver on a
+4096 x 4096 grid (mixed precision vs FP64 on the same GPU), with the relative
+error against the FP64 CPU oracle on the 512^2 stride-8 subsample, the
+dominant kernel's fraction of the measured HBM bandwidth, an end-to-end
+(host buffers) number, and the oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one complete solve (all seven kernels) of one 4096^2 density.
+For N > 1 (torchrun, one rank per GPU) every rank solves its own densities
+(independent problems, no data-path collective): weak scaling.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "potential solves/s at 4096² (mixed vs FP64, same GPU) at rel err≤1e-6; %HBM peak"
+WL = dict(n=4096, L=64.0, P=8.0, n_r=64, n_theta=256, count=16, seed=3)
+WORKLOAD_NAME = ("rho=|u|^2, u = 16 seeded complex Gaussians, 4096^2 grid on [-64,64)^2, "
+                 "P=8, 64 radial x 256 angular nodes, kappa=2, mixed precision (ES width 8)")
+SUB = 8            # accuracy subsample stride (512^2 points)
+N_ROT = 4          # rotating input/output pairs (4 x 268 MB > L2)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle run (no accuracy / cpu_baseline keys)")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="run only warmup + the timed mixed region (for profiler launch lists)")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- oracle
+
+def oracle_sample(rho: np.ndarray, node_frac: float = 1.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample of one solve of
+    the workload: I1 on the whole grid; the type-2 sums for a fraction of the
+    polar nodes; the type-1 sums for those nodes on the 512^2 stride-8
+    subsample.  Returns (estimated seconds for one full solve, phi on the
+    subsample when node_frac == 1 else None, description)."""
+    import oracle
+
+    n, L = WL["n"], WL["L"]
+    op = oracle.OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=WL["P"], n_r=WL["n_r"],
+                             n_theta=WL["n_theta"])
+    x = oracle.grid_axis(n, L)
+    rows = np.arange(0, n, SUB)
+    t0 = time.perf_counter()
+    i1 = oracle.i1_padded_fft(rho, op)[np.ix_(rows, rows)]
+    t1 = time.perf_counter()
+    kx, ky, *_ = oracle.polar_nodes(op)
+    D = oracle.polar_weights(op)
+    m = kx.size
+    take = np.arange(0, m, max(1, int(round(1.0 / node_frac))))
+    frac = take.size / m
+    rh = oracle.rho_hat_direct(rho, x, x, kx[take], ky[take])
+    t2 = time.perf_counter()
+    i2 = oracle.i2_direct_from_coeffs(D[take] * rh, kx[take], ky[take], x[rows], x[rows])
+    t3 = time.perf_counter()
+    sub_pts = rows.size * rows.size
+    scale1 = (n * n) / sub_pts
+    est = (t1 - t0) + (t2 - t1) / frac + (t3 - t2) * scale1 / frac
+    desc = (f"one {n}^2 solve: I1 FFTs on the full grid; type-2 sums for {take.size} of {m} "
+            f"nodes (x{1 / frac:.0f}); type-1 sums for those nodes on the {rows.size}^2 stride-{SUB} "
+            f"subsample (x{scale1 / frac:.0f} to the full grid)")
+    phi = (i1 + i2) if take.size == m else None
+    return est, phi, desc, {"i1": t1 - t0, "type2": t2 - t1, "type1": t3 - t2}
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (read-only query) stamped with the host clock."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [f.strip() for f in line.split(",")]))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        win = [s for t, s in self.samples if t0 <= t <= t1 and len(s) >= 9]
+        where = "timed region"
+        if not win:
+            win = [s for _, s in self.samples if len(s) >= 9]
+            where = "whole run (no sample fell inside the timed region)"
+        if not win:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "window": "nvidia-smi unavailable"}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(s[1]) for s in win if num(s[1]) is not None]
+        mx = [num(s[2]) for s in win if num(s[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in win for i in range(4) if s[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(win), "window": where}
+
+
+# --------------------------------------------------------------------------- helpers
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("common.cuh", "kernels.cuh", "pipeline.cuh"):
+        with open(os.path.join(ROOT, "paper_1409_2014_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_bytes(stage: str, n: int, Q: int, csz: int, n_nodes: int, w: int, rsz: int) -> float:
+    """Bytes one launch of a stage must move at minimum (inputs read once,
+    outputs written once), for an n x n grid with band half-width Q."""
+    A = csz * n * (n + 1)           # half-spectrum intermediate
+    Bc = csz * n * (Q + 1)          # band columns of the row spectra
+    band = csz * (Q + 1) * (2 * Q + 1)
+    nodes = n_nodes * (8 + 2 * w * rsz + 8 + csz)  # q0, weights, D, c
+    return float({
+        "row_fwd": 8 * n * n + A + Bc,
+        "col_main": 2 * A,
+        "band_fwd": Bc + band,
+        "interp": band + nodes,
+        "spread": nodes + band,
+        "band_inv": band + Bc,
+        "row_inv": A + Bc + 8 * n * n,
+    }[stage])
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def load_traffic(stage: str, workload: str):
+    """ncu dram bytes per launch recorded for this kernel source, else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            tab = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    ent = tab.get(f"{stage}|{workload}")
+    if not ent or ent.get("kernel_hash") != kernel_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------------------- arms
+
+def dist_setup(use_cuda: bool):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+    return world, rank, local
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step one bounded oracle sample."""
+    world, rank, _ = dist_setup(False)
+    if rank != 0:
+        return
+    import synth
+
+    n, L = WL["n"], WL["L"]
+    rho = synth.density_abs2(n, n, L, L, WL["seed"], WL["count"])
+    # size the per-step sample so that warmup + steps fit in about three minutes
+    _, _, _, comp = oracle_sample(rho, node_frac=1.0 / 64)
+    budget = 180.0 / max(1, args.steps + args.warmup)
+    frac = 1.0 / 64
+    for f in (1.0, 1.0 / 4, 1.0 / 16):
+        if comp["i1"] + (comp["type2"] + comp["type1"]) * 64 * f <= budget:
+            frac = f
+            break
+    for _ in range(args.warmup):
+        oracle_sample(rho, frac)
+    ests = []
+    desc = ""
+    for _ in range(args.steps):
+        est, _, desc, _ = oracle_sample(rho, frac)
+        ests.append(est)
+    est = float(np.mean(ests))
+    value = 1.0 / est
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1000.0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "n": n, "L": L},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup(True)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1409_2014_gb300 import Plan
+    from paper_1409_2014_gb300.build import build
+    import synth
+
+    build()
+    n, L = WL["n"], WL["L"]
+    rho_np = synth.density_abs2(n, n, L, L, WL["seed"] + rank, WL["count"])
+    rho0 = torch.from_numpy(rho_np).to(dev)
+    ins = [rho0.clone() for _ in range(N_ROT)]
+    outs = [torch.empty_like(rho0) for _ in range(N_ROT)]
+    del rho0
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        import torch.distributed as dist
+
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    plan = Plan(n, lx=L, cut_radius=WL["P"], n_r=WL["n_r"], n_theta=WL["n_theta"],
+                precision="mixed", device=dev)
+    info = plan.info
+    stream = torch.cuda.current_stream(dev)
+
+    clocks = ClockSampler(local)
+    for i in range(args.warmup):
+        plan.solve(ins[i % N_ROT], outs[i % N_ROT])
+    barrier()
+    # ---- timed region: K mixed solves, per-kernel CUDA events recorded live
+    plan.profile_begin(args.steps)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
+    e0.record(stream)
+    for i in range(args.steps):
+        plan.solve(ins[i % N_ROT], outs[i % N_ROT])
+    e1.record(stream)
+    barrier()
+    tw1 = time.time()
+    ms_total = e0.elapsed_time(e1)
+    stage_ms, n_prof = plan.profile_end()
+    clk = clocks.summary(tw0, tw1)
+    clocks.stop()
+    t_max = max_over_ranks(ms_total / 1000.0)
+    value = world * args.steps / t_max
+    ms_per_step = t_max * 1000.0 / args.steps
+    if args.only_timed:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s",
+                              "ms_per_step": ms_per_step, "steps": args.steps,
+                              "stages_ms_total": stage_ms, "only_timed": True}), flush=True)
+        plan.close()
+        return
+
+    # ---- FP64 solver on the same GPU (same input), timed separately
+    plan64 = Plan(n, lx=L, cut_radius=WL["P"], n_r=WL["n_r"], n_theta=WL["n_theta"],
+                  precision="fp64", device=dev)
+    k64 = max(3, min(args.steps, 50))
+    for i in range(2):
+        plan64.solve(ins[i % N_ROT], outs[i % N_ROT])
+    barrier()
+    e0.record(stream)
+    for i in range(k64):
+        plan64.solve(ins[i % N_ROT], outs[i % N_ROT])
+    e1.record(stream)
+    barrier()
+    t64 = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
+    value64 = world * k64 / t64
+
+    # results of both paths on the first input, for the accuracy check
+    phi_mixed = plan.solve(ins[0]).cpu().numpy()
+    phi_64 = plan64.solve(ins[0]).cpu().numpy()
+    plan64.close()
+
+    # ---- end to end through the public API with host buffers
+    rho_h = torch.from_numpy(rho_np).pin_memory()
+    phi_h = torch.empty_like(rho_h).pin_memory()
+    ke = max(3, min(args.steps, 100))
+    for _ in range(2):
+        plan.solve_host(rho_h, phi_h, ins[0], outs[0])
+    barrier()
+    e0.record(stream)
+    for i in range(ke):
+        plan.solve_host(rho_h, phi_h, ins[i % N_ROT], outs[i % N_ROT])
+    e1.record(stream)
+    barrier()
+    te = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
+    e2e = {"value": world * ke / te, "unit": "solves/s", "h2d_bytes_per_step": int(rho_h.numel() * 8),
+           "d2h_bytes_per_step": int(phi_h.numel() * 8), "steps": ke}
+
+    # ---- roofline of the dominant kernel
+    csz, rsz = 8, 4
+    avg = {k: v / max(1, n_prof) for k, v in stage_ms.items()}
+    dom = max(avg, key=avg.get)
+    peak, peak_src = load_peaks()
+    alg = algorithmic_bytes(dom, n, info.band_q, csz, info.n_nodes, info.kernel_width, rsz)
+    achieved = alg / (avg[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                else "fallback 6.8 TB/s",
+                "unit": "GB/s", "frac": achieved / peak,
+                "algorithmic_bytes_per_launch": alg, "avg_ms": avg[dom],
+                "traffic": load_traffic(dom, "4096sq_mixed"),
+                "stages_ms": {k: round(v, 5) for k, v in avg.items()},
+                "stage_share": {k: round(v / sum(avg.values()), 4) for k, v in avg.items()}}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "n": n, "L": L, "P": WL["P"], "n_r": WL["n_r"],
+                   "n_theta": WL["n_theta"], "kernel_width": info.kernel_width, "band_q": info.band_q,
+                   "global_batch": world, "parallelism": f"independent solves x{world}",
+                   "l2": f"inputs larger than L2: {N_ROT} rotating 134 MB input/output pairs"},
+        "fp64": {"value": value64, "unit": "solves/s", "ms_per_step": t64 * 1000.0 / k64, "steps": k64,
+                 "dtype": "f64", "mixed_speedup": value / value64},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": args.steps * 7,
+        "clocks": clk,
+    }
+
+    if rank == 0 and not args.no_cpu_baseline:
+        est, phi_ref, desc, _ = oracle_sample(rho_np, 1.0)
+        sub = (slice(0, n, SUB), slice(0, n, SUB))
+        acc = {}
+        for name, phi in (("mixed", phi_mixed), ("fp64", phi_64)):
+            d = phi[sub] - phi_ref
+            acc[name] = {"rel_linf": float(np.abs(d).max() / np.abs(phi_ref).max()),
+                         "rel_l2": float(np.linalg.norm(d) / np.linalg.norm(phi_ref))}
+        line["accuracy_vs_oracle"] = {"subsample": f"{n // SUB}^2 stride-{SUB}", **acc}
+        line["cpu_baseline"] = {"value": 1.0 / est, "unit": "solves/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -130,6 +130,31 @@ dsnu_status dsnu_plan_destroy(dsnu_plan plan);
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* dsnu_last_error(void);
 
+/* Host-buffer variant of dsnu_solve (end-to-end use): enqueues on `stream`
+ * the copy rho_host -> rho_dev, the solve into phi_dev, and the copy
+ * phi_dev -> phi_host, and returns at once; phi_host is valid after the
+ * stream is synchronised.  rho_host/phi_host: [ny][nx] FP64 host memory
+ * (page-locked for the copies to be asynchronous); rho_dev/phi_dev:
+ * caller-owned [ny][nx] FP64 device staging buffers.  Same errors as
+ * dsnu_solve. */
+dsnu_status dsnu_solve_host(dsnu_plan plan, const double* rho_host, double* phi_host,
+                            double* rho_dev, double* phi_dev, void* stream);
+
+/* Per-kernel timing.  After dsnu_profile_begin(plan, max_solves), each of the
+ * next max_solves solves of this plan records CUDA events on its stream
+ * before its first kernel and after each of its dsnu_stage_count() kernels.
+ * dsnu_profile_end synchronises those events, adds the elapsed time of
+ * every stage over the recorded solves into stage_ms[0 .. n_stages) (ms),
+ * writes the number of recorded solves to *n_solves, and frees the events.
+ * Errors: DSNU_EINVAL (bad arguments, profiling already active / not active),
+ * DSNU_ECUDA. */
+dsnu_status dsnu_profile_begin(dsnu_plan plan, int max_solves);
+dsnu_status dsnu_profile_end(dsnu_plan plan, double* stage_ms, int n_stages, int* n_solves);
+
+/* Number of kernels one solve launches, and their names (static strings). */
+int32_t dsnu_stage_count(void);
+const char* dsnu_stage_name(int32_t stage);
+
 /* Plan introspection for tests and benchmarks (host values, no device work). */
 typedef struct {
   int32_t n_nodes;       /* n_r * n_theta */

@@ -15,6 +15,7 @@ from ._abi import (  # noqa: F401
     DSNU_FP64, DSNU_MIXED, DSNU_PARTITION_GAUSS, DSNU_PARTITION_SHARP, DsnuError,
     dsnu_last_error, dsnu_params, dsnu_plan_create, dsnu_plan_destroy, dsnu_plan_get_info,
     dsnu_set_workspace, dsnu_solve, dsnu_solve_adjoint, dsnu_status_poll, dsnu_workspace_bytes,
+    dsnu_solve_host, dsnu_profile_begin, dsnu_profile_end, dsnu_stage_count, dsnu_stage_name,
 )
 
 _PREC = {"fp64": DSNU_FP64, "mixed": DSNU_MIXED}
@@ -92,6 +93,31 @@ class Plan:
 
     def solve_adjoint(self, g, out=None):
         return self._run(dsnu_solve_adjoint, g, out)
+
+    def solve_host(self, rho_host, phi_host, rho_dev, phi_dev):
+        """Host-buffer solve: rho_host/phi_host are (pinned) CPU float64
+        tensors, rho_dev/phi_dev device staging tensors; asynchronous on the
+        current stream (synchronise before reading phi_host)."""
+        import torch
+
+        for t in (rho_host, phi_host):
+            if t.device.type != "cpu" or t.dtype != torch.float64 or tuple(t.shape) != self.shape \
+                    or not t.is_contiguous():
+                raise ValueError("host buffers must be contiguous float64 CPU tensors of the grid shape")
+        self._check_input(rho_dev)
+        self._check_input(phi_dev)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        dsnu_solve_host(self._handle, rho_host.data_ptr(), phi_host.data_ptr(), rho_dev.data_ptr(),
+                        phi_dev.data_ptr(), stream)
+        return phi_host
+
+    def profile_begin(self, max_solves: int) -> None:
+        dsnu_profile_begin(self._handle, max_solves)
+
+    def profile_end(self):
+        """{stage name: total ms} over the recorded solves, and their count."""
+        ms, n = dsnu_profile_end(self._handle)
+        return {dsnu_stage_name(i): ms[i] for i in range(len(ms))}, n
 
     def status_poll(self) -> int:
         import torch

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "DSNU_OK", 1: "DSNU_EINVAL", 2: "DSNU_ENOMEM", 3: "DSNU_ECUDA
 EXPORTED = [
     "dsnu_plan_create", "dsnu_workspace_bytes", "dsnu_set_workspace", "dsnu_solve",
     "dsnu_solve_adjoint", "dsnu_status_poll", "dsnu_plan_destroy", "dsnu_last_error",
-    "dsnu_plan_get_info",
+    "dsnu_plan_get_info", "dsnu_solve_host", "dsnu_profile_begin", "dsnu_profile_end",
+    "dsnu_stage_count", "dsnu_stage_name",
 ]
 
 
@@ -83,6 +84,17 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dsnu_last_error.restype = ctypes.c_char_p
     lib.dsnu_plan_get_info.argtypes = [vp, ctypes.POINTER(dsnu_plan_info)]
     lib.dsnu_plan_get_info.restype = st
+    lib.dsnu_solve_host.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.dsnu_solve_host.restype = st
+    lib.dsnu_profile_begin.argtypes = [vp, ctypes.c_int]
+    lib.dsnu_profile_begin.restype = st
+    lib.dsnu_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int)]
+    lib.dsnu_profile_end.restype = st
+    lib.dsnu_stage_count.argtypes = []
+    lib.dsnu_stage_count.restype = ctypes.c_int32
+    lib.dsnu_stage_name.argtypes = [ctypes.c_int32]
+    lib.dsnu_stage_name.restype = ctypes.c_char_p
     _LIB = lib
     return lib
 
@@ -138,3 +150,33 @@ def dsnu_plan_get_info(plan: int) -> dsnu_plan_info:
     info = dsnu_plan_info()
     _check(load().dsnu_plan_get_info(ctypes.c_void_p(plan), ctypes.byref(info)), "dsnu_plan_get_info")
     return info
+
+
+def dsnu_solve_host(plan: int, rho_host: int, phi_host: int, rho_dev: int, phi_dev: int,
+                    stream: int = 0) -> None:
+    _check(load().dsnu_solve_host(ctypes.c_void_p(plan), ctypes.c_void_p(rho_host),
+                                  ctypes.c_void_p(phi_host), ctypes.c_void_p(rho_dev),
+                                  ctypes.c_void_p(phi_dev), ctypes.c_void_p(stream)),
+           "dsnu_solve_host")
+
+
+def dsnu_profile_begin(plan: int, max_solves: int) -> None:
+    _check(load().dsnu_profile_begin(ctypes.c_void_p(plan), int(max_solves)), "dsnu_profile_begin")
+
+
+def dsnu_profile_end(plan: int):
+    """Returns (per-stage total ms list, number of recorded solves)."""
+    n = dsnu_stage_count()
+    arr = (ctypes.c_double * n)()
+    cnt = ctypes.c_int()
+    _check(load().dsnu_profile_end(ctypes.c_void_p(plan), arr, n, ctypes.byref(cnt)),
+           "dsnu_profile_end")
+    return list(arr), cnt.value
+
+
+def dsnu_stage_count() -> int:
+    return int(load().dsnu_stage_count())
+
+
+def dsnu_stage_name(i: int) -> str:
+    return load().dsnu_stage_name(int(i)).decode()

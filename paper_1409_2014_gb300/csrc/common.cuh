@@ -115,87 +115,116 @@ __device__ __forceinline__ void dft_rec(cpx<R> (&v)[RAD]) {
 }
 
 // ---------------------------------------------------------------------------
-// Length-N forward DFT (e^{-2 pi i nk/N}) of buf[0..N) in shared memory by the
-// G = N/16 threads t = 0..G-1 of one group; every thread of the CTA must call
-// it (it contains __syncthreads).  Stockham autosort, radix-16 stages then one
-// radix-2/4/8 stage; natural order in and out.  `tw` = e^{-2 pi i m/N}, m < N,
-// generated in FP64 on the host.  With inv = true the DFT is the inverse
-// (e^{+2 pi i nk/N}, unnormalised), computed as conj(DFT(conj x)) with the
-// conjugations folded into the first loads and the last stores.
-// The caller synchronises before the call (inputs written); the call ends
-// with a barrier (outputs visible).
+// Length-N DFT by a group of G = N/16 threads (t = 0..G-1), data in registers.
+//
+// On entry thread t holds v[m] = x[t + G m], m = 0..15; on return it holds
+// v[m] = X[t + G m] (X = DFT_N[x], e^{-2 pi i nk/N}; with inv = true the
+// unnormalised inverse e^{+2 pi i nk/N}, computed as conj(DFT(conj x))).
+// Stockham autosort: radix-16 stages, then one radix-2/4/8 stage; the first
+// stage reads the registers, the last leaves its outputs in registers, the
+// stages in between exchange through `buf` (this group's shared-memory
+// buffer of kBuf(N) elements, index i stored at i + i/16 so that every stage
+// is free of bank conflicts).  Every thread of the CTA must call it the same
+// number of times (it contains __syncthreads()).  `tw` = e^{-2 pi i m/N},
+// m < N, generated in FP64 on the host.
 // ---------------------------------------------------------------------------
+__host__ __device__ constexpr int fft_buf_elems(int n) { return n + n / 16; }
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
 template <int LOG2N, int S>
 struct StageInfo {
   static constexpr int full = LOG2N / 4;
   static constexpr int lr = (S < full) ? 4 : (LOG2N - 4 * full);
   static constexpr int nstages = (LOG2N + 3) / 4;
+  static constexpr int log2ns = 4 * S;  // product of the previous radices
 };
 
-template <typename R, int LOG2N, int LR, int LOG2NS, bool FIRST, bool LAST>
-__device__ __forceinline__ void fft_stage(cpx<R>* buf, int t, bool active,
-                                          const cpx<R>* __restrict__ tw, bool inv) {
+template <typename R, int LOG2N, int S>
+__device__ __forceinline__ void fft_stage_regs(cpx<R> (&v)[16], cpx<R>* buf, int t,
+                                               const cpx<R>* __restrict__ tw) {
+  using SI = StageInfo<LOG2N, S>;
   constexpr int N = 1 << LOG2N;
+  constexpr int LR = SI::lr;
   constexpr int RAD = 1 << LR;
   constexpr int NB = N / RAD;
   constexpr int G = N / 16;
   constexpr int PER = 16 / RAD;
+  constexpr int LOG2NS = SI::log2ns;
   constexpr int NS = 1 << LOG2NS;
-  cpx<R> v[PER][RAD];
-  if (active) {
+  constexpr bool FIRST = (S == 0);
+  constexpr bool LAST = (S == SI::nstages - 1);
+  if constexpr (!FIRST) {
+    __syncthreads();  // previous stage's stores visible
 #pragma unroll
     for (int b = 0; b < PER; ++b) {
       const int j = t + b * G;
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) {
-        cpx<R> a = buf[j + r * NB];
-        if (FIRST && inv) a.y = -a.y;
-        v[b][r] = a;
-      }
+      for (int r = 0; r < RAD; ++r) v[b * RAD + r] = buf[pad16(j + r * NB)];
     }
   }
-  __syncthreads();
-  if (active) {
+  // (stage 0 has RAD = 16, PER = 1 and v[r] = x[t + G r] = x[j + r NB] already)
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int j = t + b * G;
+    const int k = j & (NS - 1);
+    if constexpr (LOG2NS > 0) {
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        const int m = (r * k) << (LOG2N - LOG2NS - LR);
+        v[b * RAD + r] = cmul(v[b * RAD + r], tw[m]);
+      }
+    }
+    cpx<R> u[RAD];
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) u[r] = v[b * RAD + r];
+    dft_rec<RAD, R>(u);
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[b * RAD + r] = u[r];
+  }
+  if constexpr (!LAST) {
+    __syncthreads();  // every load of this buffer done (in place)
 #pragma unroll
     for (int b = 0; b < PER; ++b) {
       const int j = t + b * G;
       const int k = j & (NS - 1);
-      if constexpr (LOG2NS > 0) {
-#pragma unroll
-        for (int r = 1; r < RAD; ++r) {
-          const int m = (r * k) << (LOG2N - LOG2NS - LR);
-          v[b][r] = cmul(v[b][r], tw[m]);
-        }
-      }
-      dft_rec<RAD, R>(v[b]);
       const int base = (j - k) * RAD + k;
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) {
-        cpx<R> a = v[b][r];
-        if (LAST && inv) a.y = -a.y;
-        buf[base + r * NS] = a;
-      }
+      for (int r = 0; r < RAD; ++r) buf[pad16(base + r * NS)] = v[b * RAD + r];
     }
+  } else {
+    // slot b*RAD + r holds X[j_b + r NS] = X[t + G (b + r PER)]
+    cpx<R> o[16];
+#pragma unroll
+    for (int b = 0; b < PER; ++b)
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) o[b + r * PER] = v[b * RAD + r];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = o[m];
   }
-  __syncthreads();
 }
 
-template <typename R, int LOG2N, int S, int LOG2NS>
-__device__ __forceinline__ void fft_stages(cpx<R>* buf, int t, bool active,
-                                           const cpx<R>* __restrict__ tw, bool inv) {
-  using SI = StageInfo<LOG2N, S>;
-  if constexpr (S < SI::nstages) {
-    constexpr int LR = SI::lr;
-    fft_stage<R, LOG2N, LR, LOG2NS, S == 0, S == SI::nstages - 1>(buf, t, active, tw, inv);
-    fft_stages<R, LOG2N, S + 1, LOG2NS + LR>(buf, t, active, tw, inv);
+template <typename R, int LOG2N, int S>
+__device__ __forceinline__ void fft_stages_regs(cpx<R> (&v)[16], cpx<R>* buf, int t,
+                                                const cpx<R>* __restrict__ tw) {
+  if constexpr (S < StageInfo<LOG2N, 0>::nstages) {
+    fft_stage_regs<R, LOG2N, S>(v, buf, t, tw);
+    fft_stages_regs<R, LOG2N, S + 1>(v, buf, t, tw);
   }
 }
 
 template <typename R, int LOG2N>
-__device__ __forceinline__ void block_fft(cpx<R>* buf, int t, bool active,
-                                          const cpx<R>* __restrict__ tw, bool inv) {
-  static_assert(LOG2N >= 4 && LOG2N <= 13, "FFT length 16..8192");
-  fft_stages<R, LOG2N, 0, 0>(buf, t, active, tw, inv);
+__device__ __forceinline__ void block_fft_regs(cpx<R> (&v)[16], cpx<R>* buf, int t,
+                                               const cpx<R>* __restrict__ tw, bool inv) {
+  static_assert(LOG2N >= 4 && LOG2N <= 12, "FFT length 16..4096");
+  if (inv) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m].y = -v[m].y;
+  }
+  fft_stages_regs<R, LOG2N, 0>(v, buf, t, tw);
+  if (inv) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m].y = -v[m].y;
+  }
 }
 
 }  // namespace dsnu

@@ -27,15 +27,23 @@ struct PlanTables {
   int2* node_q0;  // n_nodes
   void* node_w;   // real, n_nodes * 2w (x weights then y weights)
   double* node_D; // n_nodes
-  int* tile_ptr;  // n_tiles + 1
-  int* tile_nodes;
+  int* tile_ptr;  // n_tiles + 1: spreading tile -> entry range
+  int* ent_node;  // per entry: node index
+  int2* ent_q0;   // per entry: stencil origin of the node
+  void* ent_w;    // real, per entry: the node's 2w ES weights
   int* status;    // one int
+};
+
+// Side stream and fork/join events owned by a plan.
+struct StreamSet {
+  cudaStream_t side;
+  cudaEvent_t fork, join;
 };
 
 // Workspace layout (offsets in bytes from the workspace base).
 struct WsLayout {
   size_t off_A, off_B, off_Bband, off_Sband, off_c, total;
-  int lda, ldb, ldq;
+  int ldqA, ldqB, ldq;  // q columns of the row-tiled A and B; band column length
 };
 
 struct PlanGeom {
@@ -46,11 +54,17 @@ struct PlanGeom {
   double scale;  // 1/(Mx My)
 };
 
-// Launchers (one translation unit per precision).
+constexpr int kStages = 7;       // kernels per solve
+constexpr int kProfEvents = 9;   // events per profiled solve (see run_pipeline)
+
+// Launchers (one translation unit per precision).  `ev`, when not NULL,
+// holds kProfEvents events recorded around the kernels.
 dsnu_status run_pipeline_f32(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
-                             const double* rho, double* phi, cudaStream_t st, int cj);
+                             const double* rho, double* phi, cudaStream_t st, int cj,
+                             const StreamSet& ss, cudaEvent_t* ev);
 dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
-                             const double* rho, double* phi, cudaStream_t st, int cj);
+                             const double* rho, double* phi, cudaStream_t st, int cj,
+                             const StreamSet& ss, cudaEvent_t* ev);
 cudaError_t prepare_kernels_f32(int log2nx, int log2ny);
 cudaError_t prepare_kernels_f64(int log2nx, int log2ny);
 
@@ -67,4 +81,7 @@ struct dsnu_plan_s {
   size_t table_bytes;
   void* ws;                 // caller-owned workspace
   size_t ws_bytes;
+  dsnu::StreamSet streams;  // side stream for the band chain
+  cudaEvent_t* prof_events; // profiling: max_solves * kProfEvents events, or NULL
+  int prof_max, prof_used;
 };

@@ -4,11 +4,11 @@
 // natural frequency index q in [0, M) with signed value q - M for q >= N.
 // Per solve, with rho real:
 //
-//   k_row_fwd : per row, z = rho + i b with b = rho * dx(x) dy(y) (ES
+//   k_row_fwd : per row, z = rho + i b with b = rho dx(x) dy(y) (ES
 //               deconvolution, the type-2 prefactor); one length-M DFT of the
-//               zero-padded z; the two real-signal spectra are separated
-//               (A = row DFT of rho for q in [0, N], B = row DFT of b for
-//               q in [0, Q]).                               [I1 and eq. 2.2 prep]
+//               zero-padded z (two length-N DFTs: even and odd q); the two
+//               real-signal spectra are separated: A = row DFT of rho for q in
+//               [0, N], B = row DFT of b for q in [0, Q].   [I1 and eq. 2.2 prep]
 //   k_col_main: per column q_x in [0, N] of A: column DFT (length M, N inputs),
 //               times m1 = (1 - p) (-k_x^2/|k|^2) (eq. SubInt1), inverse
 //               column DFT keeping N rows; in place.               [I1]
@@ -20,9 +20,15 @@
 //               spreading, eq. 2.1), gathered per tile from a node list
 //               (no atomics).
 //   k_band_inv: per band column: inverse column DFT of S, N rows.
-//   k_row_inv : per row: one inverse length-M DFT of
-//               W = Y + i S (Hermitian extension of both), keeping N points;
+//   k_row_inv : per row: one inverse length-M DFT of W = Y + i S
+//               (Hermitian extension of both), keeping N points;
 //               Phi = [Re T + Im T dx dy] / (Mx My)   (I1 + I2, eq. PotSplitWhoSpace).
+//
+// Intermediate spectra (A, B and the inverse band columns) are stored
+// row-tiled: element (row iy, column q) at [iy / TR][q][iy % TR] with TR rows
+// of 32 bytes per tile segment (TR = 4 complex floats or 2 complex doubles),
+// so that the row passes (TR rows per CTA) and the column passes (one column
+// per CTA) both move whole 32-byte sectors.
 //
 // `cj` = 1 runs the same pipeline with every complex constant conjugated
 // (DFT signs, the packing unit i, the centring phases): for real input this is
@@ -33,8 +39,6 @@
 #include "common.cuh"
 
 namespace dsnu {
-
-constexpr int kThreads = 512;  // every FFT-bearing kernel: 512 threads, 16 values per thread per FFT
 
 template <typename R>
 struct AxisTabs {
@@ -71,132 +75,201 @@ __device__ __forceinline__ R mult_high(const MultTabs<R>& mt, int qx, int qy_nat
   return -(wx2 / s) * part;
 }
 
-template <int LOG2N>
+// Row tiling of the intermediate spectra (see the file comment).
+template <typename R>
+struct Tile {
+  static constexpr int LT = (sizeof(R) == 4) ? 2 : 1;  // log2 rows per tile
+  static constexpr int TR = 1 << LT;
+  __device__ __forceinline__ static size_t at(int iy, int q, int ldq) {
+    return ((size_t(iy >> LT) * ldq + q) << LT) | size_t(iy & (TR - 1));
+  }
+};
+
+// Launch geometry shared by the kernels and their launchers.
+template <typename R, int LOG2N>
 struct Geo {
   static constexpr int N = 1 << LOG2N;
   static constexpr int M = 2 * N;
-  static constexpr int G = N / 16;          // threads per length-N FFT
-  static constexpr int PER_CTA = 4096 / N;  // rows (or columns) per CTA
+  static constexpr int G = N / 16;                   // threads per length-N FFT
+  static constexpr int FB = fft_buf_elems(N);        // one FFT buffer
+  static constexpr int RS = ((FB + 15) & ~15) + 4;   // row-buffer stride (== 4 mod 16)
+  static constexpr int TR = Tile<R>::TR;
+  // forward row pass: RB_F rows per CTA (>= TR), T_RF threads; every group
+  // of G threads transforms RB_F / (T_RF / G) rows one after the other
+  // rows per CTA for small N are capped so that shared memory stays <= ~150 KB
+  static constexpr int RMAX = (sizeof(R) == 4) ? 128 : 64;
+  static constexpr int RB_F = (TR * G >= 256) ? TR : ((256 / G < RMAX) ? 256 / G : RMAX);
+  static constexpr int T_RF = (RB_F * G > 512) ? 512 : RB_F * G;
+  static constexpr int RPG_F = RB_F / (T_RF / G);
+  // inverse row pass: RB_I rows per CTA, one group per row, two buffers per row
+  static constexpr int RB_I0 = (sizeof(R) == 4) ? ((2 * G >= 256) ? 2 : 256 / G)
+                                                : ((G >= 256) ? 1 : 256 / G);
+  static constexpr int RB_I = (RB_I0 < RMAX / 2) ? RB_I0 : RMAX / 2;
+  static constexpr int T_RI = RB_I * G;
+  // column passes: CC columns per CTA
+  static constexpr int CC = (G >= 256) ? 1 : 256 / G;
+  static constexpr int T_C = CC * G;
+  static constexpr size_t smem_row_fwd = size_t(RB_F) * RS * sizeof(cpx<R>);
+  static constexpr size_t smem_row_inv = size_t(2 * RB_I) * RS * sizeof(cpx<R>);
+  static constexpr size_t smem_col = size_t(CC) * (FB + N) * sizeof(cpx<R>);  // FFT buffer + held chain
+  static constexpr size_t smem_band_fwd = size_t(CC) * FB * sizeof(cpx<R>);
   static_assert(LOG2N >= 4 && LOG2N <= 12, "grid size 16..4096");
 };
 
-template <typename R>
-constexpr size_t fft_smem_bytes() { return size_t(2) * 4096 * sizeof(cpx<R>); }
-
 // ---------------------------------------------------------------------------
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(kThreads)
-k_row_fwd(const double* __restrict__ rho, cpx<R>* __restrict__ A, int lda,
-          cpx<R>* __restrict__ Brow, int ldb, int Q, int ny, AxisTabs<R> ax,
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RF)
+k_row_fwd(const double* __restrict__ rho, cpx<R>* __restrict__ A, int ldqA,
+          cpx<R>* __restrict__ B, int ldqB, int Q, int ny, AxisTabs<R> ax,
           const R* __restrict__ decon_y, int cj) {
-  using GG = Geo<LOG2N>;
-  constexpr int N = GG::N, G = GG::G, RPC = GG::PER_CTA;
+  using GG = Geo<R, LOG2N>;
+  constexpr int N = GG::N, G = GG::G, RB = GG::RB_F, T = GG::T_RF, RS = GG::RS;
+  constexpr int NG = T / G, RPG = GG::RPG_F;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
   const int tid = threadIdx.x;
-  const int row0 = blockIdx.x * RPC;
+  const int grp = tid / G, t = tid - grp * G;
+  const int row0 = blockIdx.x * RB;
   const R isg = cj ? R(-1) : R(1);
-  for (int idx = tid; idx < RPC * N; idx += kThreads) {
-    const int rl = idx >> LOG2N, n = idx & (N - 1), row = row0 + rl;
-    R v = R(0), b = R(0);
-    if (row < ny) {
-      v = R(rho[(size_t)row * N + n]);
-      b = v * ax.decon[n] * decon_y[row];
+#pragma unroll 1
+  for (int par = 0; par < 2; ++par) {
+#pragma unroll 1
+    for (int i = 0; i < RPG; ++i) {
+      const int rr = grp + i * NG;  // row within the CTA
+      const int row = row0 + rr;
+      const bool valid = row < ny;
+      const R dy = valid ? decon_y[row] : R(0);
+      cpx<R>* buf = sm + rr * RS;
+      cpx<R> v[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int n = t + G * m;
+        const R x = valid ? R(rho[size_t(row) * N + n]) : R(0);
+        cpx<R> z = mk<R>(x, isg * (x * ax.decon[n] * dy));
+        if (par) {
+          cpx<R> w = ax.twM[n];
+          w.y *= isg;
+          z = cmul(z, w);
+        }
+        v[m] = z;
+      }
+      block_fft_regs<R, LOG2N>(v, buf, t, ax.twN, cj != 0);
+      __syncthreads();  // last-stage loads of buf finished everywhere
+#pragma unroll
+      for (int m = 0; m < 16; ++m) buf[pad16(t + G * m)] = v[m];
     }
-    const cpx<R> z = mk<R>(v, isg * b);
-    cpx<R> w = ax.twM[n];
-    w.y *= isg;
-    sm[(2 * rl) * N + n] = z;
-    sm[(2 * rl + 1) * N + n] = cmul(z, w);
-  }
-  __syncthreads();
-  block_fft<R, LOG2N>(sm + (tid / G) * N, tid % G, true, ax.twN, cj != 0);
-  for (int idx = tid; idx < RPC * (N + 1); idx += kThreads) {
-    const int rl = idx / (N + 1), q = idx - rl * (N + 1), row = row0 + rl;
-    if (row >= ny) continue;
-    const cpx<R>* E = sm + (2 * rl) * N;
-    const cpx<R>* O = E + N;
-    const cpx<R> zq = (q & 1) ? O[q >> 1] : E[q >> 1];
-    const cpx<R> zm = (q == 0) ? E[0] : ((q & 1) ? O[N - ((q + 1) >> 1)] : E[N - (q >> 1)]);
-    A[(size_t)row * lda + q] = mk<R>(R(0.5) * (zq.x + zm.x), R(0.5) * (zq.y - zm.y));
-    if (q <= Q) {
-      const cpx<R> d = mk<R>(zq.x - zm.x, zq.y + zm.y);  // Z(q) - conj Z(M - q)
-      // divide by 2 i (2 (-i) in the conjugated pipeline)
-      Brow[(size_t)row * ldb + q] = cj ? mk<R>(R(-0.5) * d.y, R(0.5) * d.x)
-                                       : mk<R>(R(0.5) * d.y, R(-0.5) * d.x);
+    __syncthreads();
+    // separate the spectra at q = 2k + par, q in [0, N] (rows fastest)
+    const int nk = par ? N / 2 : N / 2 + 1;
+    for (int idx = tid; idx < RB * nk; idx += T) {
+      const int r2 = idx & (RB - 1), k = idx / RB, row2 = row0 + r2;
+      if (row2 >= ny) continue;
+      const cpx<R>* bb = sm + r2 * RS;
+      const int q = 2 * k + par;
+      const cpx<R> zq = bb[pad16(k)];
+      const cpx<R> zm = par ? bb[pad16(N - 1 - k)] : bb[pad16(k == 0 ? 0 : N - k)];
+      A[Tile<R>::at(row2, q, ldqA)] = mk<R>(R(0.5) * (zq.x + zm.x), R(0.5) * (zq.y - zm.y));
+      if (q <= Q) {
+        const cpx<R> d = mk<R>(zq.x - zm.x, zq.y + zm.y);  // Z(q) - conj Z(M - q)
+        // divided by 2 i (by 2 (-i) in the conjugated pipeline)
+        B[Tile<R>::at(row2, q, ldqB)] = cj ? mk<R>(R(-0.5) * d.y, R(0.5) * d.x)
+                                           : mk<R>(R(0.5) * d.y, R(-0.5) * d.x);
+      }
     }
   }
 }
 
 // ---------------------------------------------------------------------------
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(kThreads)
-k_col_main(cpx<R>* __restrict__ A, int lda, int ncols, AxisTabs<R> ay, MultTabs<R> mt, int cj) {
-  using GG = Geo<LOG2N>;
-  constexpr int N = GG::N, G = GG::G, CPC = GG::PER_CTA;
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C)
+k_col_main(cpx<R>* __restrict__ A, int ldqA, int ncols, AxisTabs<R> ay, MultTabs<R> mt, int cj) {
+  using GG = Geo<R, LOG2N>;
+  constexpr int G = GG::G, CC = GG::CC, FB = GG::FB;
+  // the odd chain's loads of this column precede its first barrier, and the
+  // even chain's result is held in shared memory, so the in-place update is safe
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
   const int tid = threadIdx.x;
-  const int c0 = blockIdx.x * CPC;
+  const int cl = tid / G, t = tid - cl * G;
+  const int col = blockIdx.x * CC + cl;
+  const bool valid = col < ncols;
   const R isg = cj ? R(-1) : R(1);
-  for (int idx = tid; idx < CPC * N; idx += kThreads) {
-    const int cl = idx & (CPC - 1), n = idx / CPC, col = c0 + cl;
-    cpx<R> x = mk<R>(R(0), R(0));
-    if (col < ncols) x = A[(size_t)n * lda + col];
-    cpx<R> w = ay.twM[n];
-    w.y *= isg;
-    sm[(2 * cl) * N + n] = x;
-    sm[(2 * cl + 1) * N + n] = cmul(x, w);
-  }
-  __syncthreads();
-  block_fft<R, LOG2N>(sm + (tid / G) * N, tid % G, true, ay.twN, cj != 0);
-  for (int idx = tid; idx < 2 * CPC * N; idx += kThreads) {
-    const int chn = idx >> LOG2N, k = idx & (N - 1);
-    const int col = c0 + (chn >> 1);
-    const R m = (col < ncols) ? mult_high(mt, col, 2 * k + (chn & 1)) : R(0);
-    sm[idx] = sm[idx] * m;
-  }
-  __syncthreads();
-  block_fft<R, LOG2N>(sm + (tid / G) * N, tid % G, true, ay.twN, cj == 0);
-  for (int idx = tid; idx < CPC * N; idx += kThreads) {
-    const int cl = idx & (CPC - 1), n = idx / CPC, col = c0 + cl;
-    if (col >= ncols) continue;
-    const cpx<R> e = sm[(2 * cl) * N + n], o = sm[(2 * cl + 1) * N + n];
-    const cpx<R> w = ay.twM[n];
-    A[(size_t)n * lda + col] = cj ? e + cmul(o, w) : e + cmulc(o, w);
+  cpx<R>* buf = sm + cl * FB;
+  cpx<R>* held = sm + CC * FB + cl * GG::N;  // even-chain result, index n
+#pragma unroll 1
+  for (int par = 0; par < 2; ++par) {
+    cpx<R> v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int n = t + G * m;
+      cpx<R> x = valid ? A[Tile<R>::at(n, col, ldqA)] : mk<R>(R(0), R(0));
+      if (par) {
+        cpx<R> w = ay.twM[n];
+        w.y *= isg;
+        x = cmul(x, w);
+      }
+      v[m] = x;
+    }
+    block_fft_regs<R, LOG2N>(v, buf, t, ay.twN, cj != 0);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int q = 2 * (t + G * m) + par;
+      v[m] = v[m] * (valid ? mult_high(mt, col, q) : R(0));
+    }
+    block_fft_regs<R, LOG2N>(v, buf, t, ay.twN, cj == 0);
+    if (par == 0) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) held[t + G * m] = v[m];
+    } else if (valid) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int n = t + G * m;
+        const cpx<R> w = ay.twM[n];
+        const cpx<R> e = held[n];
+        A[Tile<R>::at(n, col, ldqA)] = cj ? e + cmul(v[m], w) : e + cmulc(v[m], w);
+      }
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(kThreads)
-k_band_fwd(const cpx<R>* __restrict__ Brow, int ldb, int ncols, cpx<R>* __restrict__ Bband,
-           int ldq, int Q, AxisTabs<R> ay, int cj) {
-  using GG = Geo<LOG2N>;
-  constexpr int N = GG::N, M = GG::M, G = GG::G, CPC = GG::PER_CTA;
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C)
+k_band_fwd(const cpx<R>* __restrict__ B, int ldqB, int ncols, cpx<R>* __restrict__ Bband, int ldq,
+           int Q, AxisTabs<R> ay, int cj) {
+  using GG = Geo<R, LOG2N>;
+  constexpr int N = GG::N, M = GG::M, G = GG::G, CC = GG::CC, FB = GG::FB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
   const int tid = threadIdx.x;
-  const int c0 = blockIdx.x * CPC;
+  const int cl = tid / G, t = tid - cl * G;
+  const int col = blockIdx.x * CC + cl;
+  const bool valid = col < ncols;
   const R isg = cj ? R(-1) : R(1);
-  for (int idx = tid; idx < CPC * N; idx += kThreads) {
-    const int cl = idx & (CPC - 1), n = idx / CPC, col = c0 + cl;
-    cpx<R> x = mk<R>(R(0), R(0));
-    if (col < ncols) x = Brow[(size_t)n * ldb + col];
-    cpx<R> w = ay.twM[n];
-    w.y *= isg;
-    sm[(2 * cl) * N + n] = x;
-    sm[(2 * cl + 1) * N + n] = cmul(x, w);
-  }
-  __syncthreads();
-  block_fft<R, LOG2N>(sm + (tid / G) * N, tid % G, true, ay.twN, cj != 0);
-  const int nq = 2 * Q + 1;
-  for (int idx = tid; idx < CPC * nq; idx += kThreads) {
-    const int cl = idx / nq, s = idx - cl * nq - Q, col = c0 + cl;
-    if (col >= ncols) continue;
-    const int q = s < 0 ? s + M : s;
-    const cpx<R>* E = sm + (2 * cl) * N;
-    Bband[(size_t)col * ldq + s + Q] = (q & 1) ? E[N + (q >> 1)] : E[q >> 1];
+  cpx<R>* buf = sm + cl * FB;
+#pragma unroll 1
+  for (int par = 0; par < 2; ++par) {
+    cpx<R> v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int n = t + G * m;
+      cpx<R> x = valid ? B[Tile<R>::at(n, col, ldqB)] : mk<R>(R(0), R(0));
+      if (par) {
+        cpx<R> w = ay.twM[n];
+        w.y *= isg;
+        x = cmul(x, w);
+      }
+      v[m] = x;
+    }
+    block_fft_regs<R, LOG2N>(v, buf, t, ay.twN, cj != 0);
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int q = 2 * (t + G * m) + par;
+        const int s = q < N ? q : q - M;
+        if (s >= -Q && s <= Q) Bband[size_t(col) * ldq + s + Q] = v[m];
+      }
+    }
   }
 }
 
@@ -211,7 +284,7 @@ k_interp(const cpx<R>* __restrict__ Bband, int ldq, int Q, const int2* __restric
   const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (j >= n_nodes) return;
   const int2 b0 = q0[j];
-  const R* wx = wts + (size_t)j * 2 * w;
+  const R* wx = wts + size_t(j) * 2 * w;
   const R* wy = wx + w;
   R ax = R(0), ay = R(0);
   for (int p = lane; p < w * w; p += 32) {
@@ -219,9 +292,9 @@ k_interp(const cpx<R>* __restrict__ Bband, int ldq, int Q, const int2* __restric
     const int qx = b0.x + a, qy = b0.y + b;
     cpx<R> v;
     if (qx >= 0) {
-      v = Bband[(size_t)qx * ldq + qy + Q];
+      v = Bband[size_t(qx) * ldq + qy + Q];
     } else {
-      v = conj(Bband[(size_t)(-qx) * ldq + (Q - qy)]);
+      v = conj(Bband[size_t(-qx) * ldq + (Q - qy)]);
     }
     const int e = qx + qy;
     v = mul_ipow(v, cj ? -e : e);  // centring phase i^{q_x + q_y}
@@ -241,19 +314,22 @@ k_interp(const cpx<R>* __restrict__ Bband, int ldq, int Q, const int2* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Type-1 spreading as a gather: one CTA per 16 x 16 tile of band cells; the
-// nodes whose stencil meets the tile are listed at plan time.
-constexpr int kTile = 16;
+// Type-1 spreading as a gather: one CTA per 8 x 8 tile of band cells; the
+// (node, stencil origin, ES weights) entries of every node whose stencil meets
+// the tile are laid out contiguously per tile at plan time, so a chunk of 64
+// entries is fetched with independent loads.
+constexpr int kTile = 8;
 constexpr int kSpreadChunk = 64;
 
 template <typename R>
-__global__ void __launch_bounds__(256)
-k_spread(const cpx<R>* __restrict__ c, const int2* __restrict__ q0, const R* __restrict__ wts,
-         int w, const int* __restrict__ tile_ptr, const int* __restrict__ tile_nodes,
-         int tiles_x, int Q, cpx<R>* __restrict__ Sband, int ldq, int cj) {
+__global__ void __launch_bounds__(kTile * kTile)
+k_spread(const cpx<R>* __restrict__ c, const int* __restrict__ tile_ptr,
+         const int* __restrict__ ent_node, const int2* __restrict__ ent_q0,
+         const R* __restrict__ ent_w, int w, int tiles_x, int Q, cpx<R>* __restrict__ Sband,
+         int ldq, int cj) {
   __shared__ int2 s_q0[kSpreadChunk];
   __shared__ cpx<R> s_c[kSpreadChunk];
-  __shared__ R s_w[kSpreadChunk * 32];
+  __shared__ R s_w[kSpreadChunk][33];
   const int tile = blockIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   const int qx = tx * kTile + (threadIdx.x & (kTile - 1));
@@ -263,100 +339,134 @@ k_spread(const cpx<R>* __restrict__ c, const int2* __restrict__ q0, const R* __r
   const int w2 = 2 * w;
   for (int s0 = beg; s0 < end; s0 += kSpreadChunk) {
     const int cnt = min(kSpreadChunk, end - s0);
-    for (int i = threadIdx.x; i < cnt; i += 256) {
-      const int j = tile_nodes[s0 + i];
-      s_q0[i] = q0[j];
-      s_c[i] = c[j];
-    }
-    for (int i = threadIdx.x; i < cnt * w2; i += 256) {
-      const int jj = i / w2, a = i - jj * w2;
-      s_w[jj * 32 + a] = wts[(size_t)tile_nodes[s0 + jj] * w2 + a];
+    const int i = threadIdx.x;
+    if (i < cnt) {
+      s_q0[i] = ent_q0[s0 + i];
+      s_c[i] = c[ent_node[s0 + i]];
+      const R* src = ent_w + size_t(s0 + i) * w2;
+      for (int a = 0; a < w2; ++a) s_w[i][a] = src[a];
     }
     __syncthreads();
-    for (int i = 0; i < cnt; ++i) {
-      const int a = qx - s_q0[i].x, b = qy - s_q0[i].y;
+    for (int k = 0; k < cnt; ++k) {
+      const int a = qx - s_q0[k].x, b = qy - s_q0[k].y;
       if ((unsigned)a < (unsigned)w && (unsigned)b < (unsigned)w) {
-        const R f = s_w[i * 32 + a] * s_w[i * 32 + w + b];
-        ax += f * s_c[i].x;
-        ay += f * s_c[i].y;
+        const R f = s_w[k][a] * s_w[k][w + b];
+        ax += f * s_c[k].x;
+        ay += f * s_c[k].y;
       }
     }
     __syncthreads();
   }
   if (qx <= Q && qy <= Q) {
     const int e = qx + qy;
-    Sband[(size_t)qx * ldq + qy + Q] = mul_ipow(mk<R>(ax, ay), cj ? e : -e);  // (-i)^{q_x+q_y}
+    Sband[size_t(qx) * ldq + qy + Q] = mul_ipow(mk<R>(ax, ay), cj ? e : -e);  // (-i)^{q_x+q_y}
   }
 }
 
 // ---------------------------------------------------------------------------
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(kThreads)
-k_band_inv(const cpx<R>* __restrict__ Sband, int ldq, int Q, int ncols, cpx<R>* __restrict__ Scol,
-           int ldb, AxisTabs<R> ay, int cj) {
-  using GG = Geo<LOG2N>;
-  constexpr int N = GG::N, M = GG::M, G = GG::G, CPC = GG::PER_CTA;
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C)
+k_band_inv(const cpx<R>* __restrict__ Sband, int ldq, int Q, int ncols, cpx<R>* __restrict__ St,
+           int ldqB, AxisTabs<R> ay, int cj) {
+  using GG = Geo<R, LOG2N>;
+  constexpr int N = GG::N, M = GG::M, G = GG::G, CC = GG::CC, FB = GG::FB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
   const int tid = threadIdx.x;
-  const int c0 = blockIdx.x * CPC;
-  for (int idx = tid; idx < 2 * CPC * N; idx += kThreads) {
-    const int chn = idx >> LOG2N, k = idx & (N - 1);
-    const int col = c0 + (chn >> 1);
-    const int q = 2 * k + (chn & 1);
-    const int s = q < N ? q : q - M;
-    cpx<R> v = mk<R>(R(0), R(0));
-    if (col < ncols && s >= -Q && s <= Q) v = Sband[(size_t)col * ldq + s + Q];
-    sm[idx] = v;
-  }
-  __syncthreads();
-  block_fft<R, LOG2N>(sm + (tid / G) * N, tid % G, true, ay.twN, cj == 0);
-  for (int idx = tid; idx < CPC * N; idx += kThreads) {
-    const int cl = idx & (CPC - 1), n = idx / CPC, col = c0 + cl;
-    if (col >= ncols) continue;
-    const cpx<R> e = sm[(2 * cl) * N + n], o = sm[(2 * cl + 1) * N + n];
-    const cpx<R> w = ay.twM[n];
-    Scol[(size_t)n * ldb + col] = cj ? e + cmul(o, w) : e + cmulc(o, w);
+  const int cl = tid / G, t = tid - cl * G;
+  const int col = blockIdx.x * CC + cl;
+  const bool valid = col < ncols;
+  cpx<R>* buf = sm + cl * FB;
+  cpx<R>* held = sm + CC * FB + cl * N;
+#pragma unroll 1
+  for (int par = 0; par < 2; ++par) {
+    cpx<R> v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int q = 2 * (t + G * m) + par;
+      const int s = q < N ? q : q - M;
+      v[m] = (valid && s >= -Q && s <= Q) ? Sband[size_t(col) * ldq + s + Q] : mk<R>(R(0), R(0));
+    }
+    block_fft_regs<R, LOG2N>(v, buf, t, ay.twN, cj == 0);
+    if (par == 0) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) held[t + G * m] = v[m];
+    } else if (valid) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int n = t + G * m;
+        const cpx<R> w = ay.twM[n];
+        const cpx<R> e = held[n];
+        St[Tile<R>::at(n, col, ldqB)] = cj ? e + cmul(v[m], w) : e + cmulc(v[m], w);
+      }
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
+// Inverse length-M DFT keeping n < N, split by output parity:
+//   T(2j)   = IDFT_N[W(q) + W(q + N)](j)
+//   T(2j+1) = IDFT_N[(W(q) - W(q + N)) e^{+2 pi i q/M}](j),   q < N,
+// with W(q) = Y(q) + i S(q) for q <= N and W(M - q) = conj Y(q) + i conj S(q).
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(kThreads)
-k_row_inv(const cpx<R>* __restrict__ A, int lda, const cpx<R>* __restrict__ Scol, int ldb, int Q,
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI)
+k_row_inv(const cpx<R>* __restrict__ A, int ldqA, const cpx<R>* __restrict__ St, int ldqB, int Q,
           double* __restrict__ phi, int ny, AxisTabs<R> ax, const R* __restrict__ decon_y, R scale,
           int cj) {
-  using GG = Geo<LOG2N>;
-  constexpr int N = GG::N, M = GG::M, G = GG::G, RPC = GG::PER_CTA;
+  using GG = Geo<R, LOG2N>;
+  constexpr int N = GG::N, G = GG::G, RB = GG::RB_I, T = GG::T_RI, RS = GG::RS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
   const int tid = threadIdx.x;
-  const int row0 = blockIdx.x * RPC;
+  const int rr = tid / G, t = tid - rr * G;
+  const int row0 = blockIdx.x * RB;
+  const int row = row0 + rr;
   const int si = cj ? -1 : 1;
-  for (int idx = tid; idx < RPC * M; idx += kThreads) {
-    const int rl = idx >> (LOG2N + 1), q = idx & (M - 1), row = row0 + rl;
-    cpx<R> W = mk<R>(R(0), R(0));
-    if (row < ny) {
-      const bool lo = q <= N;
-      const int qq = lo ? q : M - q;
-      cpx<R> y = A[(size_t)row * lda + qq];
-      cpx<R> s = (qq <= Q) ? Scol[(size_t)row * ldb + qq] : mk<R>(R(0), R(0));
-      if (!lo) { y = conj(y); s = conj(s); }
-      W = y + mul_i(s, si);
+  // U (sum) buffers of the RB rows, then V (difference) buffers
+  for (int idx = tid; idx < RB * N; idx += T) {
+    const int r2 = idx & (RB - 1), q = idx / RB, row2 = row0 + r2;
+    cpx<R> u = mk<R>(R(0), R(0)), d = mk<R>(R(0), R(0));
+    if (row2 < ny) {
+      // W(q), q in [0, N)
+      cpx<R> y = A[Tile<R>::at(row2, q, ldqA)];
+      cpx<R> s = (q <= Q) ? St[Tile<R>::at(row2, q, ldqB)] : mk<R>(R(0), R(0));
+      const cpx<R> wlo = y + mul_i(s, si);
+      // W(q + N): q = 0 -> W(N) = Y(N) + i S(N); else conj of the mirror N - q
+      const int qm = (q == 0) ? N : N - q;
+      y = A[Tile<R>::at(row2, qm, ldqA)];
+      s = (qm <= Q) ? St[Tile<R>::at(row2, qm, ldqB)] : mk<R>(R(0), R(0));
+      if (q != 0) {
+        y = conj(y);
+        s = conj(s);
+      }
+      const cpx<R> whi = y + mul_i(s, si);
+      u = wlo + whi;
+      cpx<R> w = ax.twM[q];  // e^{-2 pi i q/M}; the inverse uses its conjugate
+      d = wlo - whi;
+      d = cj ? cmul(d, w) : cmulc(d, w);
     }
-    sm[(2 * rl + (q & 1)) * N + (q >> 1)] = W;
+    sm[r2 * RS + pad16(q)] = u;
+    sm[(RB + r2) * RS + pad16(q)] = d;
   }
   __syncthreads();
-  block_fft<R, LOG2N>(sm + (tid / G) * N, tid % G, true, ax.twN, cj == 0);
-  for (int idx = tid; idx < RPC * N; idx += kThreads) {
-    const int rl = idx >> LOG2N, n = idx & (N - 1), row = row0 + rl;
-    if (row >= ny) continue;
-    const cpx<R> e = sm[(2 * rl) * N + n], o = sm[(2 * rl + 1) * N + n];
-    const cpx<R> w = ax.twM[n];
-    const cpx<R> T = cj ? e + cmul(o, w) : e + cmulc(o, w);
-    const R im = cj ? -T.y : T.y;
-    const R val = (T.x + im * ax.decon[n] * decon_y[row]) * scale;
-    phi[(size_t)row * N + n] = double(val);
+  const bool valid = row < ny;
+  const R dy = valid ? decon_y[row] : R(0);
+#pragma unroll 1
+  for (int par = 0; par < 2; ++par) {
+    cpx<R>* buf = sm + (par * RB + rr) * RS;
+    cpx<R> v[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = buf[pad16(t + G * m)];
+    block_fft_regs<R, LOG2N>(v, buf, t, ax.twN, cj == 0);
+    if (valid) {
+      // slot m holds T(2 (t + G m) + par); the grid keeps n < N, i.e. m < 8
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int n = 2 * (t + G * m) + par;
+        const R im = cj ? -v[m].y : v[m].y;
+        phi[size_t(row) * N + n] = double((v[m].x + im * ax.decon[n] * dy) * scale);
+      }
+    }
   }
 }
 

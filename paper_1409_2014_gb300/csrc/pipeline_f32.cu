@@ -3,8 +3,9 @@
 
 namespace dsnu {
 dsnu_status run_pipeline_f32(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
-                             const double* rho, double* phi, cudaStream_t st, int cj) {
-  return run_pipeline<float>(g, t, L, ws, rho, phi, st, cj);
+                             const double* rho, double* phi, cudaStream_t st, int cj,
+                             const StreamSet& ss, cudaEvent_t* ev) {
+  return run_pipeline<float>(g, t, L, ws, rho, phi, st, cj, ss, ev);
 }
 cudaError_t prepare_kernels_f32(int log2nx, int log2ny) { return prepare_kernels<float>(log2nx, log2ny); }
 }  // namespace dsnu

@@ -118,7 +118,9 @@ struct HostTables {
   std::vector<int2> node_q0;
   std::vector<R> node_w;
   std::vector<double> node_D;
-  std::vector<int> tile_ptr, tile_nodes;
+  std::vector<int> tile_ptr, ent_node;
+  std::vector<int2> ent_q0;
+  std::vector<R> ent_w;
 };
 
 static void twiddles(int n, int m, std::vector<double>& out) {
@@ -229,17 +231,19 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
     return fail(DSNU_EINVAL, "disk plus ES stencil does not fit the padded grid: need P*h + w*pi/M < pi");
   g.Q = Q;
 
-  // spreading tiles over q_x in [0, Q], q_y in [-Q, Q]
-  g.tiles_x = (Q + 1 + 15) / 16;
-  g.tiles_y = (2 * Q + 1 + 15) / 16;
+  // spreading tiles (kTile x kTile cells) over q_x in [0, Q], q_y in [-Q, Q];
+  // per tile, the entries of every node whose stencil meets it
+  const int TS = 8;
+  g.tiles_x = (Q + 1 + TS - 1) / TS;
+  g.tiles_y = (2 * Q + 1 + TS - 1) / TS;
   g.n_tiles = g.tiles_x * g.tiles_y;
   std::vector<std::vector<int>> lists(g.n_tiles);
   for (int j = 0; j < nn; ++j) {
     const int xlo = std::max(T.node_q0[j].x, 0), xhi = std::min(T.node_q0[j].x + w - 1, Q);
     if (xhi < xlo) continue;
     const int ylo = T.node_q0[j].y + Q, yhi = T.node_q0[j].y + w - 1 + Q;
-    for (int ty = ylo / 16; ty <= yhi / 16; ++ty)
-      for (int tx = xlo / 16; tx <= xhi / 16; ++tx) lists[ty * g.tiles_x + tx].push_back(j);
+    for (int ty = ylo / TS; ty <= yhi / TS; ++ty)
+      for (int tx = xlo / TS; tx <= xhi / TS; ++tx) lists[ty * g.tiles_x + tx].push_back(j);
   }
   T.tile_ptr.assign(g.n_tiles + 1, 0);
   g.max_tile_nodes = 0;
@@ -247,9 +251,22 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
     T.tile_ptr[i + 1] = T.tile_ptr[i] + int(lists[i].size());
     g.max_tile_nodes = std::max(g.max_tile_nodes, int(lists[i].size()));
   }
-  T.tile_nodes.reserve(T.tile_ptr.back() + 1);
-  for (auto& l : lists) T.tile_nodes.insert(T.tile_nodes.end(), l.begin(), l.end());
-  if (T.tile_nodes.empty()) T.tile_nodes.push_back(0);
+  const size_t n_ent = size_t(T.tile_ptr.back());
+  T.ent_node.reserve(n_ent + 1);
+  T.ent_q0.reserve(n_ent + 1);
+  T.ent_w.reserve((n_ent + 1) * 2 * w);
+  for (auto& l : lists)
+    for (int j : l) {
+      T.ent_node.push_back(j);
+      T.ent_q0.push_back(T.node_q0[j]);
+      T.ent_w.insert(T.ent_w.end(), T.node_w.begin() + size_t(j) * 2 * w,
+                     T.node_w.begin() + size_t(j + 1) * 2 * w);
+    }
+  if (T.ent_node.empty()) {
+    T.ent_node.push_back(0);
+    T.ent_q0.push_back(make_int2(0, 0));
+    T.ent_w.resize(2 * w, R(0));
+  }
 
   // one device block for every table
   Builder b;
@@ -257,7 +274,8 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   const size_t o_twNy = b.add(T.twN_y), o_twMy = b.add(T.twM_y), o_dy = b.add(T.decon_y);
   const size_t o_wx2 = b.add(T.m_wx2), o_gx = b.add(T.m_gx), o_wy2 = b.add(T.m_wy2), o_gy = b.add(T.m_gy);
   const size_t o_q0 = b.add(T.node_q0), o_w = b.add(T.node_w), o_D = b.add(T.node_D);
-  const size_t o_tp = b.add(T.tile_ptr), o_tn = b.add(T.tile_nodes);
+  const size_t o_tp = b.add(T.tile_ptr), o_en = b.add(T.ent_node), o_eq = b.add(T.ent_q0);
+  const size_t o_ew = b.add(T.ent_w);
   const int zero = 0;
   const size_t o_st = b.add(&zero, sizeof(int));
   void* dev = nullptr;
@@ -278,7 +296,9 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   t.node_w = d + o_w;
   t.node_D = reinterpret_cast<double*>(d + o_D);
   t.tile_ptr = reinterpret_cast<int*>(d + o_tp);
-  t.tile_nodes = reinterpret_cast<int*>(d + o_tn);
+  t.ent_node = reinterpret_cast<int*>(d + o_en);
+  t.ent_q0 = reinterpret_cast<int2*>(d + o_eq);
+  t.ent_w = d + o_ew;
   t.status = reinterpret_cast<int*>(d + o_st);
   P->table_block = dev;
   P->table_bytes = b.bytes.size();
@@ -289,8 +309,8 @@ static void layout_workspace(dsnu_plan_s* P) {
   const PlanGeom& g = P->geom;
   const size_t csz = (g.precision == DSNU_MIXED) ? 8 : 16;
   WsLayout& L = P->ws_layout;
-  L.lda = g.nx + 2;
-  L.ldb = (g.Q + 2) & ~1;
+  L.ldqA = g.nx + 1;
+  L.ldqB = g.Q + 1;
   L.ldq = 2 * g.Q + 1;
   size_t off = 0;
   auto take = [&](size_t n) {
@@ -298,8 +318,8 @@ static void layout_workspace(dsnu_plan_s* P) {
     off = (off + n + 255) & ~size_t(255);
     return o;
   };
-  L.off_A = take(size_t(g.ny) * L.lda * csz);
-  L.off_B = take(size_t(g.ny) * L.ldb * csz);
+  L.off_A = take(size_t(g.ny) * L.ldqA * csz);
+  L.off_B = take(size_t(g.ny) * L.ldqB * csz);
   L.off_Bband = take(size_t(g.Q + 1) * L.ldq * csz);
   L.off_Sband = take(size_t(g.Q + 1) * L.ldq * csz);
   L.off_c = take(size_t(g.n_nodes) * csz);
@@ -367,6 +387,14 @@ dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan*
     return fail(DSNU_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
   }
   layout_workspace(P);
+  cudaError_t se = cudaStreamCreateWithFlags(&P->streams.side, cudaStreamNonBlocking);
+  if (se == cudaSuccess) se = cudaEventCreateWithFlags(&P->streams.fork, cudaEventDisableTiming);
+  if (se == cudaSuccess) se = cudaEventCreateWithFlags(&P->streams.join, cudaEventDisableTiming);
+  if (se != cudaSuccess) {
+    cudaFree(P->table_block);
+    delete P;
+    return fail(DSNU_ECUDA, std::string("stream/event creation: ") + cudaGetErrorString(se));
+  }
   *out = P;
   return DSNU_OK;
 }
@@ -391,9 +419,22 @@ static dsnu_status run(dsnu_plan plan, const double* in, double* out, void* stre
   const char* b = reinterpret_cast<const char*>(out);
   if (a < b + nbytes && b < a + nbytes) return fail(DSNU_EINVAL, "input and output overlap");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t* ev = nullptr;
+  if (plan->prof_events && plan->prof_used < plan->prof_max)
+    ev = plan->prof_events + size_t(plan->prof_used++) * kProfEvents;
   if (plan->geom.precision == DSNU_MIXED)
-    return run_pipeline_f32(plan->geom, plan->tab, plan->ws_layout, plan->ws, in, out, st, cj);
-  return run_pipeline_f64(plan->geom, plan->tab, plan->ws_layout, plan->ws, in, out, st, cj);
+    return run_pipeline_f32(plan->geom, plan->tab, plan->ws_layout, plan->ws, in, out, st, cj,
+                            plan->streams, ev);
+  return run_pipeline_f64(plan->geom, plan->tab, plan->ws_layout, plan->ws, in, out, st, cj,
+                          plan->streams, ev);
+}
+
+static void free_profile(dsnu_plan plan) {
+  if (!plan->prof_events) return;
+  for (int i = 0; i < plan->prof_max * kProfEvents; ++i) cudaEventDestroy(plan->prof_events[i]);
+  delete[] plan->prof_events;
+  plan->prof_events = nullptr;
+  plan->prof_max = plan->prof_used = 0;
 }
 
 dsnu_status dsnu_solve(dsnu_plan plan, const double* rho, double* phi, void* stream) {
@@ -417,10 +458,81 @@ dsnu_status dsnu_status_poll(dsnu_plan plan, void* stream) {
 
 dsnu_status dsnu_plan_destroy(dsnu_plan plan) {
   if (!plan) return DSNU_OK;
+  free_profile(plan);
+  cudaStreamSynchronize(plan->streams.side);
+  cudaEventDestroy(plan->streams.fork);
+  cudaEventDestroy(plan->streams.join);
+  cudaStreamDestroy(plan->streams.side);
   cudaError_t e = cudaFree(plan->table_block);
   delete plan;
   if (e != cudaSuccess) return fail(DSNU_ECUDA, std::string("cudaFree: ") + cudaGetErrorString(e));
   return DSNU_OK;
+}
+
+dsnu_status dsnu_solve_host(dsnu_plan plan, const double* rho_host, double* phi_host, double* rho_dev,
+                            double* phi_dev, void* stream) {
+  if (!plan) return fail(DSNU_EINVAL, "NULL plan");
+  if (!rho_host || !phi_host || !rho_dev || !phi_dev) return fail(DSNU_EINVAL, "NULL buffer");
+  const size_t nbytes = size_t(plan->geom.nx) * plan->geom.ny * sizeof(double);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(rho_dev, rho_host, nbytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(DSNU_ECUDA, std::string("H2D copy: ") + cudaGetErrorString(e));
+  const dsnu_status s = run(plan, rho_dev, phi_dev, stream, 0);
+  if (s != DSNU_OK) return s;
+  e = cudaMemcpyAsync(phi_host, phi_dev, nbytes, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return fail(DSNU_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(e));
+  return DSNU_OK;
+}
+
+dsnu_status dsnu_profile_begin(dsnu_plan plan, int max_solves) {
+  if (!plan || max_solves < 1 || max_solves > (1 << 20)) return fail(DSNU_EINVAL, "bad plan or max_solves");
+  if (plan->prof_events) return fail(DSNU_EINVAL, "profiling already active");
+  const int n = max_solves * kProfEvents;
+  cudaEvent_t* ev = new (std::nothrow) cudaEvent_t[n];
+  if (!ev) return fail(DSNU_ENOMEM, "host allocation failed");
+  for (int i = 0; i < n; ++i) {
+    const cudaError_t e = cudaEventCreate(&ev[i]);
+    if (e != cudaSuccess) {
+      for (int k = 0; k < i; ++k) cudaEventDestroy(ev[k]);
+      delete[] ev;
+      return fail(DSNU_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+    }
+  }
+  plan->prof_events = ev;
+  plan->prof_max = max_solves;
+  plan->prof_used = 0;
+  return DSNU_OK;
+}
+
+dsnu_status dsnu_profile_end(dsnu_plan plan, double* stage_ms, int n_stages, int* n_solves) {
+  if (!plan || !stage_ms || n_stages < kStages) return fail(DSNU_EINVAL, "bad arguments");
+  if (!plan->prof_events) return fail(DSNU_EINVAL, "profiling not active");
+  for (int k = 0; k < kStages; ++k) stage_ms[k] = 0.0;
+  dsnu_status st = DSNU_OK;
+  // stage k runs between events (from[k], to[k]) of a solve (see run_pipeline)
+  static const int from[kStages] = {0, 1, 1, 3, 4, 5, 7};
+  static const int to[kStages] = {1, 2, 3, 4, 5, 6, 8};
+  for (int s = 0; s < plan->prof_used && st == DSNU_OK; ++s) {
+    cudaEvent_t* ev = plan->prof_events + size_t(s) * kProfEvents;
+    cudaError_t e = cudaEventSynchronize(ev[kProfEvents - 1]);
+    for (int k = 0; k < kStages && e == cudaSuccess; ++k) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[from[k]], ev[to[k]]);
+      stage_ms[k] += ms;
+    }
+    if (e != cudaSuccess) st = fail(DSNU_ECUDA, std::string("profile events: ") + cudaGetErrorString(e));
+  }
+  if (n_solves) *n_solves = plan->prof_used;
+  free_profile(plan);
+  return st;
+}
+
+int32_t dsnu_stage_count(void) { return kStages; }
+
+const char* dsnu_stage_name(int32_t stage) {
+  static const char* names[kStages] = {"row_fwd", "col_main", "band_fwd", "interp",
+                                       "spread", "band_inv", "row_inv"};
+  return (stage >= 0 && stage < kStages) ? names[stage] : "";
 }
 
 dsnu_status dsnu_plan_get_info(dsnu_plan plan, dsnu_plan_info* info) {

@@ -158,3 +158,34 @@ def test_repeat_calls_bitwise_identical():
     b = plan.solve(rho)
     assert torch.equal(a, b)
     plan.close()
+
+
+def test_solve_host_matches_device():
+    from paper_1409_2014_gb300 import Plan
+
+    n = 128
+    rho = synth.density_sum(n, n, 16.0, 16.0, seed=8, count=4)
+    plan = Plan(n, lx=16.0, cut_radius=4.0, n_r=32, n_theta=64, precision="mixed")
+    d_in = torch.from_numpy(rho).cuda()
+    ref = plan.solve(d_in).cpu()
+    h_in = torch.from_numpy(rho).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    plan.solve_host(h_in, h_out, torch.empty_like(d_in), torch.empty_like(d_in))
+    torch.cuda.synchronize()
+    assert torch.equal(h_out, ref)
+    plan.close()
+
+
+def test_profile_reports_every_stage():
+    from paper_1409_2014_gb300 import Plan, dsnu_stage_count
+
+    n = 256
+    rho = torch.from_numpy(synth.density_sum(n, n, 16.0, 16.0, seed=4, count=5)).cuda()
+    plan = Plan(n, lx=16.0, cut_radius=6.0, n_r=32, n_theta=64, precision="mixed")
+    plan.profile_begin(3)
+    for _ in range(5):
+        plan.solve(rho)
+    stages, cnt = plan.profile_end()
+    assert cnt == 3 and len(stages) == dsnu_stage_count() == 7
+    assert all(v > 0 for v in stages.values())
+    plan.close()
