@@ -155,6 +155,30 @@ dsnu_status dsnu_profile_end(dsnu_plan plan, double* stage_ms, int n_stages, int
 int32_t dsnu_stage_count(void);
 const char* dsnu_stage_name(int32_t stage);
 
+/* Solve without any device allocation by the caller or the library.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (or any allocating routine) when they solve, e.g.
+ * code running under an allocator that forbids new device allocations, or a
+ * host loop that must not allocate after start-up.  It computes exactly what
+ * dsnu_solve computes, but its scratch is a fixed array compiled into the
+ * library (dsnu_noalloc_scratch_bytes() = 32 MiB on every GPU that loads the
+ * library, held until the process exits) instead of the plan's workspace; no
+ * workspace needs to be attached.  Enough for grids up to 1024 x 1024 in
+ * either precision; a plan needing more scratch gets DSNU_EINVAL with a
+ * message naming both sizes.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array,
+ * which keeps the previous call's contents (nothing in it needs clearing):
+ * calls whose work overlaps on the GPU (other streams, other threads, other
+ * plans) race on it and must be serialised by the caller.
+ * rho_dev, phi_dev, stream: as in dsnu_solve.  Errors: as dsnu_solve, plus
+ * DSNU_EINVAL when the plan needs more than the static scratch. */
+dsnu_status dsnu_solve_noalloc(dsnu_plan plan, const double* rho_dev, double* phi_dev, void* stream);
+
+/* Size in bytes of the static scratch used by dsnu_solve_noalloc. */
+size_t dsnu_noalloc_scratch_bytes(void);
+
 /* Plan introspection for tests and benchmarks (host values, no device work). */
 typedef struct {
   int32_t n_nodes;       /* n_r * n_theta */

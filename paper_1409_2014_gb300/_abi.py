@@ -24,7 +24,7 @@ EXPORTED = [
     "dsnu_plan_create", "dsnu_workspace_bytes", "dsnu_set_workspace", "dsnu_solve",
     "dsnu_solve_adjoint", "dsnu_status_poll", "dsnu_plan_destroy", "dsnu_last_error",
     "dsnu_plan_get_info", "dsnu_solve_host", "dsnu_profile_begin", "dsnu_profile_end",
-    "dsnu_stage_count", "dsnu_stage_name",
+    "dsnu_stage_count", "dsnu_stage_name", "dsnu_solve_noalloc", "dsnu_noalloc_scratch_bytes",
 ]
 
 
@@ -95,6 +95,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dsnu_stage_count.restype = ctypes.c_int32
     lib.dsnu_stage_name.argtypes = [ctypes.c_int32]
     lib.dsnu_stage_name.restype = ctypes.c_char_p
+    lib.dsnu_solve_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.dsnu_solve_noalloc.restype = st
+    lib.dsnu_noalloc_scratch_bytes.argtypes = []
+    lib.dsnu_noalloc_scratch_bytes.restype = ctypes.c_size_t
     _LIB = lib
     return lib
 
@@ -180,3 +184,15 @@ def dsnu_stage_count() -> int:
 
 def dsnu_stage_name(i: int) -> str:
     return load().dsnu_stage_name(int(i)).decode()
+
+
+def dsnu_solve_noalloc(plan: int, rho_ptr: int, phi_ptr: int, stream: int = 0) -> None:
+    """dsnu_solve with the library's static scratch instead of a workspace
+    (for callers that cannot allocate device memory when they solve)."""
+    _check(load().dsnu_solve_noalloc(ctypes.c_void_p(plan), ctypes.c_void_p(rho_ptr),
+                                     ctypes.c_void_p(phi_ptr), ctypes.c_void_p(stream)),
+           "dsnu_solve_noalloc")
+
+
+def dsnu_noalloc_scratch_bytes() -> int:
+    return int(load().dsnu_noalloc_scratch_bytes())
