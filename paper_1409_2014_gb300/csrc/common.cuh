@@ -123,13 +123,32 @@ __device__ __forceinline__ void dft_rec(cpx<R> (&v)[RAD]) {
 // Stockham autosort: radix-16 stages, then one radix-2/4/8 stage; the first
 // stage reads the registers, the last leaves its outputs in registers, the
 // stages in between exchange through `buf` (this group's shared-memory
-// buffer of kBuf(N) elements, index i stored at i + i/16 so that every stage
-// is free of bank conflicts).  Every thread of the CTA must call it the same
-// number of times (it contains __syncthreads()).  `tw` = e^{-2 pi i m/N},
-// m < N, generated in FP64 on the host.
+// buffer of fft_buf_elems(N) elements, index i stored at i + i/16 so that
+// every stage is free of bank conflicts).  Every thread of the CTA must call
+// it the same number of times (it contains __syncthreads()).
+//
+// `stw` (normally in shared memory) holds the twiddles of stages 1.. in the
+// order stage, r = 1..RAD-1, k = 0..NS-1:  e^{-2 pi i r k / (NS RAD)}, so that
+// threads with consecutive k read consecutive entries.  They are generated in
+// FP64 on the host (fft_stage_twiddles in plan.cu).
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int fft_buf_elems(int n) { return n + n / 16; }
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+// Offset of stage `stage`'s twiddles in the stage table of a length-2^log2n
+// transform (stages >= 1), and the table's total length (host + device).
+__host__ __device__ constexpr int fft_stage_tw_offset(int log2n, int stage) {
+  int total = 0;
+  const int full = log2n / 4;
+  for (int s = 1; s < stage; ++s) {
+    const int lr = (s < full) ? 4 : (log2n - 4 * full);
+    total += ((1 << lr) - 1) * (1 << (4 * s));
+  }
+  return total;
+}
+__host__ __device__ constexpr int fft_stage_tw_elems(int log2n) {
+  return fft_stage_tw_offset(log2n, (log2n + 3) / 4);
+}
 
 template <int LOG2N, int S>
 struct StageInfo {
@@ -137,11 +156,12 @@ struct StageInfo {
   static constexpr int lr = (S < full) ? 4 : (LOG2N - 4 * full);
   static constexpr int nstages = (LOG2N + 3) / 4;
   static constexpr int log2ns = 4 * S;  // product of the previous radices
+  static constexpr int tw_off = fft_stage_tw_offset(LOG2N, S);
 };
 
 template <typename R, int LOG2N, int S>
 __device__ __forceinline__ void fft_stage_regs(cpx<R> (&v)[16], cpx<R>* buf, int t,
-                                               const cpx<R>* __restrict__ tw) {
+                                               const cpx<R>* __restrict__ stw) {
   using SI = StageInfo<LOG2N, S>;
   constexpr int N = 1 << LOG2N;
   constexpr int LR = SI::lr;
@@ -168,11 +188,9 @@ __device__ __forceinline__ void fft_stage_regs(cpx<R> (&v)[16], cpx<R>* buf, int
     const int j = t + b * G;
     const int k = j & (NS - 1);
     if constexpr (LOG2NS > 0) {
+      const cpx<R>* tws = stw + SI::tw_off + k;
 #pragma unroll
-      for (int r = 1; r < RAD; ++r) {
-        const int m = (r * k) << (LOG2N - LOG2NS - LR);
-        v[b * RAD + r] = cmul(v[b * RAD + r], tw[m]);
-      }
+      for (int r = 1; r < RAD; ++r) v[b * RAD + r] = cmul(v[b * RAD + r], tws[(r - 1) * NS]);
     }
     cpx<R> u[RAD];
 #pragma unroll
@@ -205,26 +223,95 @@ __device__ __forceinline__ void fft_stage_regs(cpx<R> (&v)[16], cpx<R>* buf, int
 
 template <typename R, int LOG2N, int S>
 __device__ __forceinline__ void fft_stages_regs(cpx<R> (&v)[16], cpx<R>* buf, int t,
-                                                const cpx<R>* __restrict__ tw) {
+                                                const cpx<R>* __restrict__ stw) {
   if constexpr (S < StageInfo<LOG2N, 0>::nstages) {
-    fft_stage_regs<R, LOG2N, S>(v, buf, t, tw);
-    fft_stages_regs<R, LOG2N, S + 1>(v, buf, t, tw);
+    fft_stage_regs<R, LOG2N, S>(v, buf, t, stw);
+    fft_stages_regs<R, LOG2N, S + 1>(v, buf, t, stw);
   }
 }
 
 template <typename R, int LOG2N>
 __device__ __forceinline__ void block_fft_regs(cpx<R> (&v)[16], cpx<R>* buf, int t,
-                                               const cpx<R>* __restrict__ tw, bool inv) {
+                                               const cpx<R>* __restrict__ stw, bool inv) {
   static_assert(LOG2N >= 4 && LOG2N <= 12, "FFT length 16..4096");
   if (inv) {
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m].y = -v[m].y;
   }
-  fft_stages_regs<R, LOG2N, 0>(v, buf, t, tw);
+  fft_stages_regs<R, LOG2N, 0>(v, buf, t, stw);
   if (inv) {
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m].y = -v[m].y;
   }
+}
+
+// Cooperative copy of `n` table entries from global to shared memory.
+template <typename T>
+__device__ __forceinline__ void copy_to_smem(T* __restrict__ dst, const T* __restrict__ src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// FP64 <-> FP32 conversions in integer arithmetic (IEEE-754 binary64/binary32
+// bit layouts).  On GB300 the hardware conversion instructions issue on the
+// FP64 pipe, which runs at a small fraction of the FP32 rate; these run on the
+// integer pipes.  f64 -> f32 rounds to nearest even for results in the normal
+// float range, flushes results below 2^-126 to a signed zero and overflows to
+// infinity; f32 -> f64 is exact for normal floats, flushes float subnormals to
+// zero and maps infinities/NaNs to infinities/NaNs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float f64_to_f32_bits(double d) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned int hi = static_cast<unsigned int>(b >> 32);
+  const unsigned int lo = static_cast<unsigned int>(b);
+  const unsigned int sign = hi & 0x80000000u;
+  const int e = static_cast<int>((hi >> 20) & 0x7FFu) - 1023 + 127;
+  const unsigned int m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);  // top 23 mantissa bits
+  const unsigned int rest = lo & 0x1FFFFFFFu;                   // dropped 29 bits
+  unsigned int r = (static_cast<unsigned int>(e) << 23) + m;
+  r += (rest > 0x10000000u) || (rest == 0x10000000u && (m & 1u));  // nearest, ties to even
+  r = (e <= 0) ? 0u : r;
+  r = (e >= 255) ? 0x7F800000u : r;
+  return __uint_as_float(sign | r);
+}
+
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int sign = u & 0x80000000u;
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned int m = u & 0x7FFFFFu;
+  const unsigned int e64 = (e == 255u) ? 2047u : (e + (1023u - 127u));
+  unsigned int hi = sign | (e64 << 20) | (m >> 3);
+  unsigned int lo = m << 29;
+  hi = (e == 0u) ? sign : hi;
+  lo = (e == 0u) ? 0u : lo;
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+
+// Conversions used at the FP64 boundary of the pipeline (identity for double).
+template <typename R>
+__device__ __forceinline__ R from_f64(double d) {
+  if constexpr (sizeof(R) == 4) return f64_to_f32_bits(d);
+  else return d;
+}
+template <typename R>
+__device__ __forceinline__ double to_f64(R v) {
+  if constexpr (sizeof(R) == 4) return f32_to_f64_bits(v);
+  else return v;
+}
+
+// expm1 in the working precision (library function).
+template <typename R>
+__device__ __forceinline__ R expm1_r(R x) {
+  if constexpr (sizeof(R) == 4) return expm1f(x);
+  else return expm1(x);
+}
+
+// a / b: fast reciprocal path in FP32 (<= 2 ulp), IEEE division in FP64.
+template <typename R>
+__device__ __forceinline__ R fdiv(R a, R b) {
+  if constexpr (sizeof(R) == 4) return __fdividef(a, b);
+  else return a / b;
 }
 
 }  // namespace dsnu

@@ -14,16 +14,17 @@ namespace dsnu {
 // Device tables of a plan.  Real-valued tables are in the plan's working
 // precision (float for DSNU_MIXED, double for DSNU_FP64); node_D is FP64.
 struct PlanTables {
-  void* twN_x;    // cpx, nx   e^{-2 pi i m/nx}
-  void* twM_x;    // cpx, nx   e^{-2 pi i n/Mx}
+  void* stw_x;    // cpx, FFT stage twiddles of length nx (fft_stage_tw_elems)
+  void* twm_lo_x; // cpx, e^{-2 pi i n/Mx}, n < Lx = min(64, nx)
+  void* twm_hi_x; // cpx, e^{-2 pi i Lx j/Mx}, j < nx/Lx
   void* decon_x;  // real, nx  phi_hat(0)/phi_hat(2 pi (n - nx/2)/Mx)
-  void* twN_y;
-  void* twM_y;
+  void* stw_y;
+  void* twm_lo_y;
+  void* twm_hi_y;
   void* decon_y;
-  void* m_wx2;    // real, nx + 1
-  void* m_gx;     // real, nx + 1
-  void* m_wy2;    // real, My
-  void* m_gy;     // real, My
+  void* m_wx2;    // real, nx + 1  (q_x dk_x)^2
+  void* m_gx;     // real, nx + 1  1 - exp(-(q_x dk_x)^2/sigma^2)
+  void* m_gy;     // real, n_gy    1 - exp(-(a dk_y)^2/sigma^2), a < n_gy
   int2* node_q0;  // n_nodes
   void* node_w;   // real, n_nodes * 2w (x weights then y weights)
   double* node_D; // n_nodes
@@ -48,6 +49,10 @@ struct WsLayout {
 
 struct PlanGeom {
   int nx, ny, mx, my, log2nx, log2ny;
+  int log2lo_x, log2lo_y;  // two-level e^{-2 pi i n/M} tables
+  int n_gy;                // entries of the short partition table
+  double dky2;             // dk_y^2
+  int grid_rowf, grid_col, grid_bandf, grid_bandi, grid_rowi;  // persistent grid sizes
   int w, Q, n_nodes, n_tiles, tiles_x, tiles_y, max_tile_nodes;
   int precision, sharp;
   double beta, sigma, cut_radius;
@@ -65,8 +70,9 @@ dsnu_status run_pipeline_f32(const PlanGeom& g, const PlanTables& t, const WsLay
 dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
                              const double* rho, double* phi, cudaStream_t st, int cj,
                              const StreamSet& ss, cudaEvent_t* ev);
-cudaError_t prepare_kernels_f32(int log2nx, int log2ny);
-cudaError_t prepare_kernels_f64(int log2nx, int log2ny);
+// Set the kernels' shared-memory limits and compute persistent grid sizes.
+cudaError_t prepare_kernels_f32(PlanGeom& g);
+cudaError_t prepare_kernels_f64(PlanGeom& g);
 
 void set_last_error(const std::string& msg);
 

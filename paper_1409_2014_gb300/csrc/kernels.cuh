@@ -38,41 +38,66 @@
 
 #include "common.cuh"
 
+// Occupancy targets (minimum resident CTAs per SM) and the FP32 forward-row
+// tile height; overridable at compile time for tuning sweeps.
+#ifndef DSNU_ROW_MINB
+#define DSNU_ROW_MINB 2
+#endif
+#ifndef DSNU_COL_MINB
+#define DSNU_COL_MINB 2
+#endif
+#ifndef DSNU_ROWF_RB32
+#define DSNU_ROWF_RB32 2
+#endif
+
 namespace dsnu {
 
 template <typename R>
 struct AxisTabs {
-  const cpx<R>* twN;   // e^{-2 pi i m/N}, m < N
-  const cpx<R>* twM;   // e^{-2 pi i n/M}, n < N
-  const R* decon;      // phi_hat(0) / phi_hat(2 pi (n - N/2)/M), n < N
+  const cpx<R>* stw;     // FFT stage twiddles (fft_stage_twiddles), copied to shared memory
+  const cpx<R>* twm_lo;  // e^{-2 pi i n/M}, n < L  (L = min(64, N))
+  const cpx<R>* twm_hi;  // e^{-2 pi i L j/M}, j < N/L
+  int log2lo;            // log2 L
+  const R* decon;        // phi_hat(0) / phi_hat(2 pi (n - N/2)/M), n < N
 };
+
+// e^{-2 pi i n/M} for n < N from the two short tables (one complex product).
+template <typename R>
+__device__ __forceinline__ cpx<R> twm(const AxisTabs<R>& a, int n) {
+  return cmul(a.twm_hi[n >> a.log2lo], a.twm_lo[n & ((1 << a.log2lo) - 1)]);
+}
 
 template <typename R>
 struct MultTabs {
-  const R* wx2;  // (q_x dk_x)^2, q_x in [0, nx]
-  const R* gx;   // 1 - exp(-(q_x dk_x)^2 / sigma^2)
-  const R* wy2;  // (qbar_y dk_y)^2, natural q_y in [0, My)
-  const R* gy;
-  int sharp;     // 1: p = indicator of |k| <= P
-  R cut2;        // P^2
+  const R* wx2;       // (q_x dk_x)^2, q_x in [0, nx]
+  const R* gx;        // 1 - exp(-(q_x dk_x)^2 / sigma^2)
+  int n_gy;           // 1 - exp(-(a dk_y)^2 / sigma^2) rounds to 1 for a = |qbar_y| >= n_gy
+  R inv_sigma2;       // 1 / sigma^2
+  R dky2;             // dk_y^2
+  int half_my;        // N_y (= M_y / 2)
+  int sharp;          // 1: p = indicator of |k| <= P
+  R cut2;             // P^2
 };
 
-// m1 = -(k_x^2/|k|^2) (1 - p(k)), m1(0) = 0.  With the Gaussian partition
+// m1 = -(k_x^2/|k|^2) (1 - p(k)), m1(0) = 0, at column q_x and natural row
+// frequency q (signed qbar = q or q - M_y).  With the Gaussian partition
 // 1 - p = 1 - e^{-kx^2/s^2} e^{-ky^2/s^2} = gx + gy (1 - gx), a sum of
 // non-negative terms (no cancellation near k = 0).
 template <typename R>
-__device__ __forceinline__ R mult_high(const MultTabs<R>& mt, int qx, int qy_nat) {
-  const R wx2 = mt.wx2[qx], wy2 = mt.wy2[qy_nat];
+__device__ __forceinline__ R mult_high(const MultTabs<R>& mt, R wx2, R gx, int q) {
+  const int a = (q < mt.half_my) ? q : 2 * mt.half_my - q;
+  const R wy2 = R(a * a) * mt.dky2;
   const R s = wx2 + wy2;
   if (s == R(0)) return R(0);
   R part;
   if (mt.sharp) {
     part = (s > mt.cut2) ? R(1) : R(0);
   } else {
-    const R gx = mt.gx[qx], gy = mt.gy[qy_nat];
+    // 1 - exp(-ky^2/s^2): below working precision of 1 only for a < n_gy
+    const R gy = (a < mt.n_gy) ? -expm1_r(-wy2 * mt.inv_sigma2) : R(1);
     part = gx + gy * (R(1) - gx);
   }
-  return -(wx2 / s) * part;
+  return -fdiv(wx2, s) * part;
 }
 
 // Row tiling of the intermediate spectra (see the file comment).
@@ -84,6 +109,12 @@ struct Tile {
     return ((size_t(iy >> LT) * ldq + q) << LT) | size_t(iy & (TR - 1));
   }
 };
+
+// Minimum resident CTAs per SM requested from the compiler: the FP64 kernels
+// are limited to one CTA per SM by shared memory anyway, so they get the full
+// register file.
+template <typename R>
+constexpr int min_blocks(int fp32_target) { return sizeof(R) == 4 ? fp32_target : 1; }
 
 // Launch geometry shared by the kernels and their launchers.
 template <typename R, int LOG2N>
@@ -98,10 +129,11 @@ struct Geo {
   // of G threads transforms RB_F / (T_RF / G) rows one after the other
   // rows per CTA for small N are capped so that shared memory stays <= ~150 KB
   static constexpr int RMAX = (sizeof(R) == 4) ? 128 : 64;
-  static constexpr int RB_F = (TR * G >= 256) ? TR : ((256 / G < RMAX) ? 256 / G : RMAX);
+  static constexpr int RB_F0 = (sizeof(R) == 4) ? DSNU_ROWF_RB32 : TR;
+  static constexpr int RB_F = (RB_F0 * G >= 256) ? RB_F0 : ((256 / G < RMAX) ? 256 / G : RMAX);
   static constexpr int T_RF = (RB_F * G > 512) ? 512 : RB_F * G;
   static constexpr int RPG_F = RB_F / (T_RF / G);
-  // inverse row pass: RB_I rows per CTA, one group per row, two buffers per row
+  // inverse row pass: RB_I rows per CTA, one group per row
   static constexpr int RB_I0 = (sizeof(R) == 4) ? ((2 * G >= 256) ? 2 : 256 / G)
                                                 : ((G >= 256) ? 1 : 256 / G);
   static constexpr int RB_I = (RB_I0 < RMAX / 2) ? RB_I0 : RMAX / 2;
@@ -109,16 +141,22 @@ struct Geo {
   // column passes: CC columns per CTA
   static constexpr int CC = (G >= 256) ? 1 : 256 / G;
   static constexpr int T_C = CC * G;
-  static constexpr size_t smem_row_fwd = size_t(RB_F) * RS * sizeof(cpx<R>);
-  static constexpr size_t smem_row_inv = size_t(2 * RB_I) * RS * sizeof(cpx<R>);
-  static constexpr size_t smem_col = size_t(CC) * (FB + N) * sizeof(cpx<R>);  // FFT buffer + held chain
-  static constexpr size_t smem_band_fwd = size_t(CC) * FB * sizeof(cpx<R>);
+  static constexpr int STW = fft_stage_tw_elems(LOG2N) > 0 ? fft_stage_tw_elems(LOG2N) : 1;
+  static constexpr int STWP = (STW + 1) & ~1;  // keep the buffers 16-byte aligned
+  static constexpr size_t smem_row_fwd = size_t(STWP + RB_F * RS) * sizeof(cpx<R>);
+  static constexpr size_t smem_row_inv = size_t(STWP + RB_I * RS) * sizeof(cpx<R>);
+  static constexpr size_t smem_col = size_t(STWP + CC * (FB + N)) * sizeof(cpx<R>);  // + held chain
+  static constexpr size_t smem_band_fwd = size_t(STWP + CC * FB) * sizeof(cpx<R>);
   static_assert(LOG2N >= 4 && LOG2N <= 12, "grid size 16..4096");
 };
 
+// Every FFT kernel is persistent: a grid of at most (SMs x resident CTAs)
+// loops over its work items (row blocks or column blocks) and keeps the FFT
+// stage twiddles in shared memory for the whole launch.
+
 // ---------------------------------------------------------------------------
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RF)
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RF, min_blocks<R>(DSNU_ROW_MINB))
 k_row_fwd(const double* __restrict__ rho, cpx<R>* __restrict__ A, int ldqA,
           cpx<R>* __restrict__ B, int ldqB, int Q, int ny, AxisTabs<R> ax,
           const R* __restrict__ decon_y, int cj) {
@@ -126,107 +164,124 @@ k_row_fwd(const double* __restrict__ rho, cpx<R>* __restrict__ A, int ldqA,
   constexpr int N = GG::N, G = GG::G, RB = GG::RB_F, T = GG::T_RF, RS = GG::RS;
   constexpr int NG = T / G, RPG = GG::RPG_F;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* sm = stw + GG::STWP;
+  copy_to_smem(stw, ax.stw, GG::STW);
   const int tid = threadIdx.x;
   const int grp = tid / G, t = tid - grp * G;
-  const int row0 = blockIdx.x * RB;
   const R isg = cj ? R(-1) : R(1);
+  const int items = (ny + RB - 1) / RB;
 #pragma unroll 1
-  for (int par = 0; par < 2; ++par) {
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int row0 = item * RB;
 #pragma unroll 1
-    for (int i = 0; i < RPG; ++i) {
-      const int rr = grp + i * NG;  // row within the CTA
-      const int row = row0 + rr;
-      const bool valid = row < ny;
-      const R dy = valid ? decon_y[row] : R(0);
-      cpx<R>* buf = sm + rr * RS;
+    for (int par = 0; par < 2; ++par) {
+#pragma unroll 1
+      for (int i = 0; i < RPG; ++i) {
+        const int rr = grp + i * NG;  // row within the CTA
+        const int row = row0 + rr;
+        const bool valid = row < ny;
+        const R dy = valid ? decon_y[row] : R(0);
+        cpx<R>* buf = sm + rr * RS;
+        cpx<R> v[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const int n = t + G * m;
+          const R x = valid ? from_f64<R>(rho[size_t(row) * N + n]) : R(0);
+          cpx<R> z = mk<R>(x, isg * (x * ax.decon[n] * dy));
+          if (par) {
+            cpx<R> w = twm(ax, n);
+            w.y *= isg;
+            z = cmul(z, w);
+          }
+          v[m] = z;
+        }
+        block_fft_regs<R, LOG2N>(v, buf, t, stw, cj != 0);
+        __syncthreads();  // last-stage loads of buf (and the previous unpack) finished
+#pragma unroll
+        for (int m = 0; m < 16; ++m) buf[pad16(t + G * m)] = v[m];
+      }
+      __syncthreads();
+      // separate the spectra at q = 2k + par, q in [0, N] (rows fastest)
+      const int nk = par ? N / 2 : N / 2 + 1;
+      for (int idx = tid; idx < RB * nk; idx += T) {
+        const int r2 = idx & (RB - 1), k = idx / RB, row2 = row0 + r2;
+        if (row2 >= ny) continue;
+        const cpx<R>* bb = sm + r2 * RS;
+        const int q = 2 * k + par;
+        const cpx<R> zq = bb[pad16(k)];
+        const cpx<R> zm = par ? bb[pad16(N - 1 - k)] : bb[pad16(k == 0 ? 0 : N - k)];
+        A[Tile<R>::at(row2, q, ldqA)] = mk<R>(R(0.5) * (zq.x + zm.x), R(0.5) * (zq.y - zm.y));
+        if (q <= Q) {
+          const cpx<R> d = mk<R>(zq.x - zm.x, zq.y + zm.y);  // Z(q) - conj Z(M - q)
+          // divided by 2 i (by 2 (-i) in the conjugated pipeline)
+          B[Tile<R>::at(row2, q, ldqB)] = cj ? mk<R>(R(-0.5) * d.y, R(0.5) * d.x)
+                                             : mk<R>(R(0.5) * d.y, R(-0.5) * d.x);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass of I1: per column, both chains (even/odd output rows of the
+// padded column DFT) go forward, are multiplied by m1 and come back; the even
+// chain's result is held in shared memory until the odd one is done.  The odd
+// chain's loads of a column precede its first barrier, so the in-place update
+// is safe.
+template <typename R, int LOG2N>
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
+k_col_main(cpx<R>* __restrict__ A, int ldqA, int ncols, AxisTabs<R> ay, MultTabs<R> mt, int cj) {
+  using GG = Geo<R, LOG2N>;
+  constexpr int N = GG::N, G = GG::G, CC = GG::CC, FB = GG::FB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* sm = stw + GG::STWP;
+  copy_to_smem(stw, ay.stw, GG::STW);
+  const int tid = threadIdx.x;
+  const int cl = tid / G, t = tid - cl * G;
+  const R isg = cj ? R(-1) : R(1);
+  cpx<R>* buf = sm + cl * FB;
+  cpx<R>* held = sm + CC * FB + cl * N;  // even-chain result, index n
+  const int items = (ncols + CC - 1) / CC;
+#pragma unroll 1
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int col = item * CC + cl;
+    const bool valid = col < ncols;
+    const R wx2 = valid ? mt.wx2[col] : R(0);
+    const R gx = valid ? mt.gx[col] : R(0);
+#pragma unroll 1
+    for (int par = 0; par < 2; ++par) {
       cpx<R> v[16];
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int n = t + G * m;
-        const R x = valid ? R(rho[size_t(row) * N + n]) : R(0);
-        cpx<R> z = mk<R>(x, isg * (x * ax.decon[n] * dy));
+        cpx<R> x = valid ? A[Tile<R>::at(n, col, ldqA)] : mk<R>(R(0), R(0));
         if (par) {
-          cpx<R> w = ax.twM[n];
+          cpx<R> w = twm(ay, n);
           w.y *= isg;
-          z = cmul(z, w);
+          x = cmul(x, w);
         }
-        v[m] = z;
+        v[m] = x;
       }
-      block_fft_regs<R, LOG2N>(v, buf, t, ax.twN, cj != 0);
-      __syncthreads();  // last-stage loads of buf finished everywhere
-#pragma unroll
-      for (int m = 0; m < 16; ++m) buf[pad16(t + G * m)] = v[m];
-    }
-    __syncthreads();
-    // separate the spectra at q = 2k + par, q in [0, N] (rows fastest)
-    const int nk = par ? N / 2 : N / 2 + 1;
-    for (int idx = tid; idx < RB * nk; idx += T) {
-      const int r2 = idx & (RB - 1), k = idx / RB, row2 = row0 + r2;
-      if (row2 >= ny) continue;
-      const cpx<R>* bb = sm + r2 * RS;
-      const int q = 2 * k + par;
-      const cpx<R> zq = bb[pad16(k)];
-      const cpx<R> zm = par ? bb[pad16(N - 1 - k)] : bb[pad16(k == 0 ? 0 : N - k)];
-      A[Tile<R>::at(row2, q, ldqA)] = mk<R>(R(0.5) * (zq.x + zm.x), R(0.5) * (zq.y - zm.y));
-      if (q <= Q) {
-        const cpx<R> d = mk<R>(zq.x - zm.x, zq.y + zm.y);  // Z(q) - conj Z(M - q)
-        // divided by 2 i (by 2 (-i) in the conjugated pipeline)
-        B[Tile<R>::at(row2, q, ldqB)] = cj ? mk<R>(R(-0.5) * d.y, R(0.5) * d.x)
-                                           : mk<R>(R(0.5) * d.y, R(-0.5) * d.x);
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C)
-k_col_main(cpx<R>* __restrict__ A, int ldqA, int ncols, AxisTabs<R> ay, MultTabs<R> mt, int cj) {
-  using GG = Geo<R, LOG2N>;
-  constexpr int G = GG::G, CC = GG::CC, FB = GG::FB;
-  // the odd chain's loads of this column precede its first barrier, and the
-  // even chain's result is held in shared memory, so the in-place update is safe
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
-  const int tid = threadIdx.x;
-  const int cl = tid / G, t = tid - cl * G;
-  const int col = blockIdx.x * CC + cl;
-  const bool valid = col < ncols;
-  const R isg = cj ? R(-1) : R(1);
-  cpx<R>* buf = sm + cl * FB;
-  cpx<R>* held = sm + CC * FB + cl * GG::N;  // even-chain result, index n
-#pragma unroll 1
-  for (int par = 0; par < 2; ++par) {
-    cpx<R> v[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int n = t + G * m;
-      cpx<R> x = valid ? A[Tile<R>::at(n, col, ldqA)] : mk<R>(R(0), R(0));
-      if (par) {
-        cpx<R> w = ay.twM[n];
-        w.y *= isg;
-        x = cmul(x, w);
-      }
-      v[m] = x;
-    }
-    block_fft_regs<R, LOG2N>(v, buf, t, ay.twN, cj != 0);
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int q = 2 * (t + G * m) + par;
-      v[m] = v[m] * (valid ? mult_high(mt, col, q) : R(0));
-    }
-    block_fft_regs<R, LOG2N>(v, buf, t, ay.twN, cj == 0);
-    if (par == 0) {
-#pragma unroll
-      for (int m = 0; m < 16; ++m) held[t + G * m] = v[m];
-    } else if (valid) {
+      block_fft_regs<R, LOG2N>(v, buf, t, stw, cj != 0);
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
-        const int n = t + G * m;
-        const cpx<R> w = ay.twM[n];
-        const cpx<R> e = held[n];
-        A[Tile<R>::at(n, col, ldqA)] = cj ? e + cmul(v[m], w) : e + cmulc(v[m], w);
+        const int q = 2 * (t + G * m) + par;
+        v[m] = v[m] * (valid ? mult_high(mt, wx2, gx, q) : R(0));
+      }
+      block_fft_regs<R, LOG2N>(v, buf, t, stw, cj == 0);
+      if (par == 0) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) held[t + G * m] = v[m];
+      } else if (valid) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const int n = t + G * m;
+          const cpx<R> w = twm(ay, n);
+          const cpx<R> e = held[n];
+          A[Tile<R>::at(n, col, ldqA)] = cj ? e + cmul(v[m], w) : e + cmulc(v[m], w);
+        }
       }
     }
   }
@@ -234,40 +289,46 @@ k_col_main(cpx<R>* __restrict__ A, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
 
 // ---------------------------------------------------------------------------
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C)
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
 k_band_fwd(const cpx<R>* __restrict__ B, int ldqB, int ncols, cpx<R>* __restrict__ Bband, int ldq,
            int Q, AxisTabs<R> ay, int cj) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, M = GG::M, G = GG::G, CC = GG::CC, FB = GG::FB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* sm = stw + GG::STWP;
+  copy_to_smem(stw, ay.stw, GG::STW);
   const int tid = threadIdx.x;
   const int cl = tid / G, t = tid - cl * G;
-  const int col = blockIdx.x * CC + cl;
-  const bool valid = col < ncols;
   const R isg = cj ? R(-1) : R(1);
   cpx<R>* buf = sm + cl * FB;
+  const int items = (ncols + CC - 1) / CC;
 #pragma unroll 1
-  for (int par = 0; par < 2; ++par) {
-    cpx<R> v[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int n = t + G * m;
-      cpx<R> x = valid ? B[Tile<R>::at(n, col, ldqB)] : mk<R>(R(0), R(0));
-      if (par) {
-        cpx<R> w = ay.twM[n];
-        w.y *= isg;
-        x = cmul(x, w);
-      }
-      v[m] = x;
-    }
-    block_fft_regs<R, LOG2N>(v, buf, t, ay.twN, cj != 0);
-    if (valid) {
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int col = item * CC + cl;
+    const bool valid = col < ncols;
+#pragma unroll 1
+    for (int par = 0; par < 2; ++par) {
+      cpx<R> v[16];
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
-        const int q = 2 * (t + G * m) + par;
-        const int s = q < N ? q : q - M;
-        if (s >= -Q && s <= Q) Bband[size_t(col) * ldq + s + Q] = v[m];
+        const int n = t + G * m;
+        cpx<R> x = valid ? B[Tile<R>::at(n, col, ldqB)] : mk<R>(R(0), R(0));
+        if (par) {
+          cpx<R> w = twm(ay, n);
+          w.y *= isg;
+          x = cmul(x, w);
+        }
+        v[m] = x;
+      }
+      block_fft_regs<R, LOG2N>(v, buf, t, stw, cj != 0);
+      if (valid) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const int q = 2 * (t + G * m) + par;
+          const int s = q < N ? q : q - M;
+          if (s >= -Q && s <= Q) Bband[size_t(col) * ldq + s + Q] = v[m];
+        }
       }
     }
   }
@@ -365,39 +426,45 @@ k_spread(const cpx<R>* __restrict__ c, const int* __restrict__ tile_ptr,
 
 // ---------------------------------------------------------------------------
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C)
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
 k_band_inv(const cpx<R>* __restrict__ Sband, int ldq, int Q, int ncols, cpx<R>* __restrict__ St,
            int ldqB, AxisTabs<R> ay, int cj) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, M = GG::M, G = GG::G, CC = GG::CC, FB = GG::FB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* sm = stw + GG::STWP;
+  copy_to_smem(stw, ay.stw, GG::STW);
   const int tid = threadIdx.x;
   const int cl = tid / G, t = tid - cl * G;
-  const int col = blockIdx.x * CC + cl;
-  const bool valid = col < ncols;
   cpx<R>* buf = sm + cl * FB;
   cpx<R>* held = sm + CC * FB + cl * N;
+  const int items = (ncols + CC - 1) / CC;
 #pragma unroll 1
-  for (int par = 0; par < 2; ++par) {
-    cpx<R> v[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int q = 2 * (t + G * m) + par;
-      const int s = q < N ? q : q - M;
-      v[m] = (valid && s >= -Q && s <= Q) ? Sband[size_t(col) * ldq + s + Q] : mk<R>(R(0), R(0));
-    }
-    block_fft_regs<R, LOG2N>(v, buf, t, ay.twN, cj == 0);
-    if (par == 0) {
-#pragma unroll
-      for (int m = 0; m < 16; ++m) held[t + G * m] = v[m];
-    } else if (valid) {
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int col = item * CC + cl;
+    const bool valid = col < ncols;
+#pragma unroll 1
+    for (int par = 0; par < 2; ++par) {
+      cpx<R> v[16];
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
-        const int n = t + G * m;
-        const cpx<R> w = ay.twM[n];
-        const cpx<R> e = held[n];
-        St[Tile<R>::at(n, col, ldqB)] = cj ? e + cmul(v[m], w) : e + cmulc(v[m], w);
+        const int q = 2 * (t + G * m) + par;
+        const int s = q < N ? q : q - M;
+        v[m] = (valid && s >= -Q && s <= Q) ? Sband[size_t(col) * ldq + s + Q] : mk<R>(R(0), R(0));
+      }
+      block_fft_regs<R, LOG2N>(v, buf, t, stw, cj == 0);
+      if (par == 0) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) held[t + G * m] = v[m];
+      } else if (valid) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const int n = t + G * m;
+          const cpx<R> w = twm(ay, n);
+          const cpx<R> e = held[n];
+          St[Tile<R>::at(n, col, ldqB)] = cj ? e + cmul(v[m], w) : e + cmulc(v[m], w);
+        }
       }
     }
   }
@@ -409,62 +476,70 @@ k_band_inv(const cpx<R>* __restrict__ Sband, int ldq, int Q, int ncols, cpx<R>* 
 //   T(2j+1) = IDFT_N[(W(q) - W(q + N)) e^{+2 pi i q/M}](j),   q < N,
 // with W(q) = Y(q) + i S(q) for q <= N and W(M - q) = conj Y(q) + i conj S(q).
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI)
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(DSNU_ROW_MINB))
 k_row_inv(const cpx<R>* __restrict__ A, int ldqA, const cpx<R>* __restrict__ St, int ldqB, int Q,
           double* __restrict__ phi, int ny, AxisTabs<R> ax, const R* __restrict__ decon_y, R scale,
           int cj) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, RB = GG::RB_I, T = GG::T_RI, RS = GG::RS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* sm = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* sm = stw + GG::STWP;
+  copy_to_smem(stw, ax.stw, GG::STW);
   const int tid = threadIdx.x;
   const int rr = tid / G, t = tid - rr * G;
-  const int row0 = blockIdx.x * RB;
-  const int row = row0 + rr;
   const int si = cj ? -1 : 1;
-  // U (sum) buffers of the RB rows, then V (difference) buffers
-  for (int idx = tid; idx < RB * N; idx += T) {
-    const int r2 = idx & (RB - 1), q = idx / RB, row2 = row0 + r2;
-    cpx<R> u = mk<R>(R(0), R(0)), d = mk<R>(R(0), R(0));
-    if (row2 < ny) {
-      // W(q), q in [0, N)
-      cpx<R> y = A[Tile<R>::at(row2, q, ldqA)];
-      cpx<R> s = (q <= Q) ? St[Tile<R>::at(row2, q, ldqB)] : mk<R>(R(0), R(0));
-      const cpx<R> wlo = y + mul_i(s, si);
-      // W(q + N): q = 0 -> W(N) = Y(N) + i S(N); else conj of the mirror N - q
-      const int qm = (q == 0) ? N : N - q;
-      y = A[Tile<R>::at(row2, qm, ldqA)];
-      s = (qm <= Q) ? St[Tile<R>::at(row2, qm, ldqB)] : mk<R>(R(0), R(0));
-      if (q != 0) {
-        y = conj(y);
-        s = conj(s);
-      }
-      const cpx<R> whi = y + mul_i(s, si);
-      u = wlo + whi;
-      cpx<R> w = ax.twM[q];  // e^{-2 pi i q/M}; the inverse uses its conjugate
-      d = wlo - whi;
-      d = cj ? cmul(d, w) : cmulc(d, w);
-    }
-    sm[r2 * RS + pad16(q)] = u;
-    sm[(RB + r2) * RS + pad16(q)] = d;
-  }
-  __syncthreads();
-  const bool valid = row < ny;
-  const R dy = valid ? decon_y[row] : R(0);
+  cpx<R>* buf = sm + rr * RS;
+  const int items = (ny + RB - 1) / RB;
 #pragma unroll 1
-  for (int par = 0; par < 2; ++par) {
-    cpx<R>* buf = sm + (par * RB + rr) * RS;
-    cpx<R> v[16];
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int row0 = item * RB;
+    const int row = row0 + rr;
+    const bool valid = row < ny;
+    const R dy = valid ? decon_y[row] : R(0);
+#pragma unroll 1
+    for (int par = 0; par < 2; ++par) {
+      __syncthreads();  // the table copy / previous transform's last-stage loads finished
+      // par 0: U(q) = W(q) + W(q + N); par 1: V(q) = (W(q) - W(q + N)) e^{+2 pi i q/M}
+      for (int idx = tid; idx < RB * N; idx += T) {
+        const int r2 = idx & (RB - 1), q = idx / RB, row2 = row0 + r2;
+        cpx<R> u = mk<R>(R(0), R(0));
+        if (row2 < ny) {
+          cpx<R> y = A[Tile<R>::at(row2, q, ldqA)];
+          cpx<R> s = (q <= Q) ? St[Tile<R>::at(row2, q, ldqB)] : mk<R>(R(0), R(0));
+          const cpx<R> wlo = y + mul_i(s, si);
+          // W(q + N): q = 0 -> W(N) = Y(N) + i S(N); else conj of the mirror N - q
+          const int qm = (q == 0) ? N : N - q;
+          y = A[Tile<R>::at(row2, qm, ldqA)];
+          s = (qm <= Q) ? St[Tile<R>::at(row2, qm, ldqB)] : mk<R>(R(0), R(0));
+          if (q != 0) {
+            y = conj(y);
+            s = conj(s);
+          }
+          const cpx<R> whi = y + mul_i(s, si);
+          if (par == 0) {
+            u = wlo + whi;
+          } else {
+            const cpx<R> w = twm(ax, q);  // e^{-2 pi i q/M}; the inverse uses its conjugate
+            const cpx<R> d = wlo - whi;
+            u = cj ? cmul(d, w) : cmulc(d, w);
+          }
+        }
+        sm[r2 * RS + pad16(q)] = u;
+      }
+      __syncthreads();
+      cpx<R> v[16];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = buf[pad16(t + G * m)];
-    block_fft_regs<R, LOG2N>(v, buf, t, ax.twN, cj == 0);
-    if (valid) {
-      // slot m holds T(2 (t + G m) + par); the grid keeps n < N, i.e. m < 8
+      for (int m = 0; m < 16; ++m) v[m] = buf[pad16(t + G * m)];
+      block_fft_regs<R, LOG2N>(v, buf, t, stw, cj == 0);
+      if (valid) {
+        // slot m holds T(2 (t + G m) + par); the grid keeps n < N, i.e. m < 8
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int n = 2 * (t + G * m) + par;
-        const R im = cj ? -v[m].y : v[m].y;
-        phi[size_t(row) * N + n] = double((v[m].x + im * ax.decon[n] * dy) * scale);
+        for (int m = 0; m < 8; ++m) {
+          const int n = 2 * (t + G * m) + par;
+          const R im = cj ? -v[m].y : v[m].y;
+          phi[size_t(row) * N + n] = to_f64<R>((v[m].x + im * ax.decon[n] * dy) * scale);
+        }
       }
     }
   }

@@ -17,31 +17,65 @@ namespace dsnu {
   case 11: CALL(11); break;   \
   case 12: CALL(12); break;
 
-template <typename R, int L2>
-cudaError_t set_fft_attrs() {
-  using GG = Geo<R, L2>;
-  cudaError_t e;
-  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  if ((e = cudaFuncSetAttribute(k_row_fwd<R, L2>, A, int(GG::smem_row_fwd)))) return e;
-  if ((e = cudaFuncSetAttribute(k_col_main<R, L2>, A, int(GG::smem_col)))) return e;
-  if ((e = cudaFuncSetAttribute(k_band_fwd<R, L2>, A, int(GG::smem_band_fwd)))) return e;
-  if ((e = cudaFuncSetAttribute(k_band_inv<R, L2>, A, int(GG::smem_col)))) return e;
-  if ((e = cudaFuncSetAttribute(k_row_inv<R, L2>, A, int(GG::smem_row_inv)))) return e;
+template <typename K>
+static cudaError_t persistent_grid(K kernel, int threads, size_t smem, int items, int* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int cap = sms * per_sm;
+  *grid = items < cap ? (items > 0 ? items : 1) : cap;
   return cudaSuccess;
 }
 
+template <typename R, int L2>
+cudaError_t prepare_rows(PlanGeom& g) {
+  using GG = Geo<R, L2>;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_row_fwd<R, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(GG::smem_row_fwd)))) return e;
+  if ((e = cudaFuncSetAttribute(k_row_inv<R, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(GG::smem_row_inv)))) return e;
+  if ((e = persistent_grid(k_row_fwd<R, L2>, GG::T_RF, GG::smem_row_fwd,
+                           (g.ny + GG::RB_F - 1) / GG::RB_F, &g.grid_rowf))) return e;
+  return persistent_grid(k_row_inv<R, L2>, GG::T_RI, GG::smem_row_inv, (g.ny + GG::RB_I - 1) / GG::RB_I,
+                         &g.grid_rowi);
+}
+
+template <typename R, int L2>
+cudaError_t prepare_cols(PlanGeom& g) {
+  using GG = Geo<R, L2>;
+  cudaError_t e;
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if ((e = cudaFuncSetAttribute(k_col_main<R, L2>, A, int(GG::smem_col)))) return e;
+  if ((e = cudaFuncSetAttribute(k_band_fwd<R, L2>, A, int(GG::smem_band_fwd)))) return e;
+  if ((e = cudaFuncSetAttribute(k_band_inv<R, L2>, A, int(GG::smem_col)))) return e;
+  if ((e = persistent_grid(k_col_main<R, L2>, GG::T_C, GG::smem_col, (g.nx + 1 + GG::CC - 1) / GG::CC,
+                           &g.grid_col))) return e;
+  if ((e = persistent_grid(k_band_fwd<R, L2>, GG::T_C, GG::smem_band_fwd, (g.Q + 1 + GG::CC - 1) / GG::CC,
+                           &g.grid_bandf))) return e;
+  return persistent_grid(k_band_inv<R, L2>, GG::T_C, GG::smem_col, (g.Q + 1 + GG::CC - 1) / GG::CC,
+                         &g.grid_bandi);
+}
+
 template <typename R>
-cudaError_t prepare_kernels(int log2nx, int log2ny) {
+cudaError_t prepare_kernels(PlanGeom& g) {
   cudaError_t e = cudaSuccess;
-  for (int l2 : {log2nx, log2ny}) {
-#define DSNU_PREP(L2) e = set_fft_attrs<R, L2>()
-    switch (l2) {
-      DSNU_LOG2_CASES(DSNU_PREP)
-      default: return cudaErrorInvalidValue;
-    }
-#undef DSNU_PREP
-    if (e != cudaSuccess) return e;
+#define DSNU_PREP_R(L2) e = prepare_rows<R, L2>(g)
+#define DSNU_PREP_C(L2) e = prepare_cols<R, L2>(g)
+  switch (g.log2nx) {
+    DSNU_LOG2_CASES(DSNU_PREP_R)
+    default: return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess) return e;
+  switch (g.log2ny) {
+    DSNU_LOG2_CASES(DSNU_PREP_C)
+    default: return cudaErrorInvalidValue;
+  }
+#undef DSNU_PREP_R
+#undef DSNU_PREP_C
   return e;
 }
 
@@ -60,12 +94,12 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
   cpx<R>* Bband = reinterpret_cast<cpx<R>*>(base + L.off_Bband);
   cpx<R>* Sband = reinterpret_cast<cpx<R>*>(base + L.off_Sband);
   cpx<R>* cn = reinterpret_cast<cpx<R>*>(base + L.off_c);
-  const AxisTabs<R> ax{static_cast<const cpx<R>*>(t.twN_x), static_cast<const cpx<R>*>(t.twM_x),
-                       static_cast<const R*>(t.decon_x)};
-  const AxisTabs<R> ay{static_cast<const cpx<R>*>(t.twN_y), static_cast<const cpx<R>*>(t.twM_y),
-                       static_cast<const R*>(t.decon_y)};
+  const AxisTabs<R> ax{static_cast<const cpx<R>*>(t.stw_x), static_cast<const cpx<R>*>(t.twm_lo_x),
+                       static_cast<const cpx<R>*>(t.twm_hi_x), g.log2lo_x, static_cast<const R*>(t.decon_x)};
+  const AxisTabs<R> ay{static_cast<const cpx<R>*>(t.stw_y), static_cast<const cpx<R>*>(t.twm_lo_y),
+                       static_cast<const cpx<R>*>(t.twm_hi_y), g.log2lo_y, static_cast<const R*>(t.decon_y)};
   const MultTabs<R> mt{static_cast<const R*>(t.m_wx2), static_cast<const R*>(t.m_gx),
-                       static_cast<const R*>(t.m_wy2), static_cast<const R*>(t.m_gy), g.sharp,
+                       g.n_gy, R(1.0 / (g.sigma * g.sigma)), R(g.dky2), g.ny, g.sharp,
                        R(g.cut_radius * g.cut_radius)};
   const R* dcy = static_cast<const R*>(t.decon_y);
   const R* wts = static_cast<const R*>(t.node_w);
@@ -73,19 +107,19 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
   cudaStream_t sd = ss.side;
 
 #define DSNU_ROWF(L2)                                                                               \
-  k_row_fwd<R, L2><<<(g.ny + Geo<R, L2>::RB_F - 1) / Geo<R, L2>::RB_F, Geo<R, L2>::T_RF,            \
+  k_row_fwd<R, L2><<<g.grid_rowf, Geo<R, L2>::T_RF,                                               \
                      Geo<R, L2>::smem_row_fwd, st>>>(rho, A, ldqA, B, ldqB, g.Q, g.ny, ax, dcy, cj)
 #define DSNU_COLM(L2)                                                                                 \
-  k_col_main<R, L2><<<(g.nx + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC, Geo<R, L2>::T_C,            \
+  k_col_main<R, L2><<<g.grid_col, Geo<R, L2>::T_C,                                                 \
                       Geo<R, L2>::smem_col, st>>>(A, ldqA, g.nx + 1, ay, mt, cj)
 #define DSNU_BANDF(L2)                                                                                \
-  k_band_fwd<R, L2><<<(g.Q + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC, Geo<R, L2>::T_C,             \
+  k_band_fwd<R, L2><<<g.grid_bandf, Geo<R, L2>::T_C,                                               \
                       Geo<R, L2>::smem_band_fwd, sd>>>(B, ldqB, g.Q + 1, Bband, L.ldq, g.Q, ay, cj)
 #define DSNU_BANDI(L2)                                                                                \
-  k_band_inv<R, L2><<<(g.Q + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC, Geo<R, L2>::T_C,             \
+  k_band_inv<R, L2><<<g.grid_bandi, Geo<R, L2>::T_C,                                               \
                       Geo<R, L2>::smem_col, sd>>>(Sband, L.ldq, g.Q, g.Q + 1, B, ldqB, ay, cj)
 #define DSNU_ROWI(L2)                                                                                 \
-  k_row_inv<R, L2><<<(g.ny + Geo<R, L2>::RB_I - 1) / Geo<R, L2>::RB_I, Geo<R, L2>::T_RI,            \
+  k_row_inv<R, L2><<<g.grid_rowi, Geo<R, L2>::T_RI,                                                \
                      Geo<R, L2>::smem_row_inv, st>>>(A, ldqA, B, ldqB, g.Q, phi, g.ny, ax, dcy,     \
                                                      R(g.scale), cj)
 #define DSNU_MARK(I, S) \

@@ -7,5 +7,5 @@ dsnu_status run_pipeline_f32(const PlanGeom& g, const PlanTables& t, const WsLay
                              const StreamSet& ss, cudaEvent_t* ev) {
   return run_pipeline<float>(g, t, L, ws, rho, phi, st, cj, ss, ev);
 }
-cudaError_t prepare_kernels_f32(int log2nx, int log2ny) { return prepare_kernels<float>(log2nx, log2ny); }
+cudaError_t prepare_kernels_f32(PlanGeom& g) { return prepare_kernels<float>(g); }
 }  // namespace dsnu

@@ -7,5 +7,5 @@ dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLay
                              const StreamSet& ss, cudaEvent_t* ev) {
   return run_pipeline<double>(g, t, L, ws, rho, phi, st, cj, ss, ev);
 }
-cudaError_t prepare_kernels_f64(int log2nx, int log2ny) { return prepare_kernels<double>(log2nx, log2ny); }
+cudaError_t prepare_kernels_f64(PlanGeom& g) { return prepare_kernels<double>(g); }
 }  // namespace dsnu

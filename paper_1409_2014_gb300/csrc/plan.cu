@@ -24,6 +24,7 @@
 #include <string>
 #include <vector>
 
+#include "common.cuh"
 #include "internal.h"
 
 namespace dsnu {
@@ -113,8 +114,9 @@ struct EsFourier {
 
 template <typename R>
 struct HostTables {
-  std::vector<R> twN_x, twM_x, decon_x, twN_y, twM_y, decon_y;  // twiddles interleaved re, im
-  std::vector<R> m_wx2, m_gx, m_wy2, m_gy;
+  // complex tables interleaved (re, im)
+  std::vector<R> stw_x, twm_lo_x, twm_hi_x, decon_x, stw_y, twm_lo_y, twm_hi_y, decon_y;
+  std::vector<R> m_wx2, m_gx, m_gy;
   std::vector<int2> node_q0;
   std::vector<R> node_w;
   std::vector<double> node_D;
@@ -130,6 +132,42 @@ static void twiddles(int n, int m, std::vector<double>& out) {
     out[2 * i] = std::cos(a);
     out[2 * i + 1] = std::sin(a);
   }
+}
+
+// FFT stage twiddles of a length-2^log2n transform in the order the device
+// FFT reads them: stage s >= 1 (radix RAD, NS = product of the earlier
+// radices), r = 1..RAD-1, k = 0..NS-1: e^{-2 pi i r k / (NS RAD)}.
+static void fft_stage_twiddles(int log2n, std::vector<double>& out) {
+  out.clear();
+  const int full = log2n / 4;
+  const int nst = (log2n + 3) / 4;
+  for (int s = 1; s < nst; ++s) {
+    const int lr = (s < full) ? 4 : (log2n - 4 * full);
+    const int rad = 1 << lr, ns = 1 << (4 * s);
+    for (int r = 1; r < rad; ++r)
+      for (int k = 0; k < ns; ++k) {
+        const double a = -2.0 * M_PI * double(r) * double(k) / double(ns * rad);
+        out.push_back(std::cos(a));
+        out.push_back(std::sin(a));
+      }
+  }
+  if (out.empty()) out.assign(2, 0.0);
+}
+
+// e^{-2 pi i n/M}, n < N, as a product of two short tables:
+// lo[i] = e^{-2 pi i i/M} (i < L), hi[j] = e^{-2 pi i L j/M} (j < N/L), L = min(64, N).
+static int half_angle_tables(int n, std::vector<double>& lo, std::vector<double>& hi) {
+  const int L = n < 64 ? n : 64;
+  twiddles(L, 2 * n, lo);
+  hi.resize(2 * (n / L));
+  for (int j = 0; j < n / L; ++j) {
+    const double a = -2.0 * M_PI * double(L) * double(j) / double(2 * n);
+    hi[2 * j] = std::cos(a);
+    hi[2 * j + 1] = std::sin(a);
+  }
+  int l = 0;
+  while ((1 << l) < L) ++l;
+  return l;
 }
 
 template <typename R>
@@ -180,17 +218,22 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   EsFourier fh(w, beta);
   const double ph0 = fh(0.0);
   HostTables<R> T;
-  std::vector<double> tmp;
-  twiddles(nx, nx, tmp); T.twN_x = cast<R>(tmp);
-  twiddles(nx, Mx, tmp); T.twM_x = cast<R>(tmp);
-  twiddles(ny, ny, tmp); T.twN_y = cast<R>(tmp);
-  twiddles(ny, My, tmp); T.twM_y = cast<R>(tmp);
+  std::vector<double> tmp, tmp2;
+  fft_stage_twiddles(g.log2nx, tmp); T.stw_x = cast<R>(tmp);
+  fft_stage_twiddles(g.log2ny, tmp); T.stw_y = cast<R>(tmp);
+  if (int(T.stw_x.size()) != 2 * std::max(1, fft_stage_tw_elems(g.log2nx)) ||
+      int(T.stw_y.size()) != 2 * std::max(1, fft_stage_tw_elems(g.log2ny)))
+    return fail(DSNU_EINVAL, "internal: stage twiddle table size mismatch");
+  g.log2lo_x = half_angle_tables(nx, tmp, tmp2); T.twm_lo_x = cast<R>(tmp); T.twm_hi_x = cast<R>(tmp2);
+  g.log2lo_y = half_angle_tables(ny, tmp, tmp2); T.twm_lo_y = cast<R>(tmp); T.twm_hi_y = cast<R>(tmp2);
   T.decon_x.resize(nx);
   for (int n = 0; n < nx; ++n) T.decon_x[n] = R(ph0 / fh(2.0 * M_PI * (n - nx / 2) / Mx));
   T.decon_y.resize(ny);
   for (int n = 0; n < ny; ++n) T.decon_y[n] = R(ph0 / fh(2.0 * M_PI * (n - ny / 2) / My));
 
-  // multiplier axis tables
+  // multiplier axis tables: per column q_x; along y only the partition factor
+  // 1 - exp(-(a dk_y)^2/sigma^2) up to the first |qbar_y| = a where it is 1 in
+  // working precision ((a dk_y)^2 itself is formed in the kernel)
   T.m_wx2.resize(nx + 1);
   T.m_gx.resize(nx + 1);
   for (int q = 0; q <= nx; ++q) {
@@ -198,14 +241,17 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
     T.m_wx2[q] = R(a * a);
     T.m_gx[q] = R(-std::expm1(-(a * a) / (sigma * sigma)));
   }
-  T.m_wy2.resize(My);
-  T.m_gy.resize(My);
-  for (int q = 0; q < My; ++q) {
-    const int qs = q < ny ? q : q - My;
-    const double a = qs * dky;
-    T.m_wy2[q] = R(a * a);
-    T.m_gy[q] = R(-std::expm1(-(a * a) / (sigma * sigma)));
+  g.dky2 = dky * dky;
+  T.m_gy.clear();
+  if (!g.sharp) {
+    for (int a = 0; a <= ny; ++a) {
+      const double v = -std::expm1(-(a * dky) * (a * dky) / (sigma * sigma));
+      if (R(v) == R(1)) break;
+      T.m_gy.push_back(R(v));
+    }
   }
+  g.n_gy = int(T.m_gy.size());
+  if (T.m_gy.empty()) T.m_gy.push_back(R(0));
 
   // per-node stencils
   T.node_q0.resize(nn);
@@ -270,9 +316,11 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
 
   // one device block for every table
   Builder b;
-  const size_t o_twNx = b.add(T.twN_x), o_twMx = b.add(T.twM_x), o_dx = b.add(T.decon_x);
-  const size_t o_twNy = b.add(T.twN_y), o_twMy = b.add(T.twM_y), o_dy = b.add(T.decon_y);
-  const size_t o_wx2 = b.add(T.m_wx2), o_gx = b.add(T.m_gx), o_wy2 = b.add(T.m_wy2), o_gy = b.add(T.m_gy);
+  const size_t o_stx = b.add(T.stw_x), o_tlx = b.add(T.twm_lo_x), o_thx = b.add(T.twm_hi_x);
+  const size_t o_dx = b.add(T.decon_x);
+  const size_t o_sty = b.add(T.stw_y), o_tly = b.add(T.twm_lo_y), o_thy = b.add(T.twm_hi_y);
+  const size_t o_dy = b.add(T.decon_y);
+  const size_t o_wx2 = b.add(T.m_wx2), o_gx = b.add(T.m_gx), o_gy = b.add(T.m_gy);
   const size_t o_q0 = b.add(T.node_q0), o_w = b.add(T.node_w), o_D = b.add(T.node_D);
   const size_t o_tp = b.add(T.tile_ptr), o_en = b.add(T.ent_node), o_eq = b.add(T.ent_q0);
   const size_t o_ew = b.add(T.ent_w);
@@ -289,9 +337,9 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   }
   char* d = static_cast<char*>(dev);
   PlanTables& t = P->tab;
-  t.twN_x = d + o_twNx; t.twM_x = d + o_twMx; t.decon_x = d + o_dx;
-  t.twN_y = d + o_twNy; t.twM_y = d + o_twMy; t.decon_y = d + o_dy;
-  t.m_wx2 = d + o_wx2; t.m_gx = d + o_gx; t.m_wy2 = d + o_wy2; t.m_gy = d + o_gy;
+  t.stw_x = d + o_stx; t.twm_lo_x = d + o_tlx; t.twm_hi_x = d + o_thx; t.decon_x = d + o_dx;
+  t.stw_y = d + o_sty; t.twm_lo_y = d + o_tly; t.twm_hi_y = d + o_thy; t.decon_y = d + o_dy;
+  t.m_wx2 = d + o_wx2; t.m_gx = d + o_gx; t.m_gy = d + o_gy;
   t.node_q0 = reinterpret_cast<int2*>(d + o_q0);
   t.node_w = d + o_w;
   t.node_D = reinterpret_cast<double*>(d + o_D);
@@ -379,8 +427,7 @@ dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan*
     delete P;
     return s;
   }
-  const cudaError_t e = (p.precision == DSNU_MIXED) ? prepare_kernels_f32(g.log2nx, g.log2ny)
-                                                    : prepare_kernels_f64(g.log2nx, g.log2ny);
+  const cudaError_t e = (p.precision == DSNU_MIXED) ? prepare_kernels_f32(g) : prepare_kernels_f64(g);
   if (e != cudaSuccess) {
     cudaFree(P->table_block);
     delete P;
