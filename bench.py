@@ -7,7 +7,7 @@ dominant kernel's fraction of the measured HBM bandwidth, an end-to-end
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One step = one complete solve (all seven kernels) of one 4096^2 density.
+One step = one complete solve (all eight kernels) of one 4096^2 density.
 For N > 1 (torchrun, one rank per GPU) every rank solves its own densities
 (independent problems, no data-path collective): weak scaling.
 """
@@ -156,7 +156,8 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def algorithmic_bytes(stage: str, n: int, Q: int, csz: int, n_nodes: int, w: int, rsz: int) -> float:
+def algorithmic_bytes(stage: str, n: int, Q: int, csz: int, n_nodes: int, w: int, rsz: int,
+                      n_items: int = 0) -> float:
     """Bytes one launch of a stage must move at minimum (inputs read once,
     outputs written once), for an n x n grid with band half-width Q."""
     A = csz * n * (n + 1)           # half-spectrum intermediate
@@ -168,7 +169,8 @@ def algorithmic_bytes(stage: str, n: int, Q: int, csz: int, n_nodes: int, w: int
         "col_main": 2 * A,
         "band_fwd": Bc + band,
         "interp": band + nodes,
-        "spread": nodes + band,
+        "spread": nodes + n_items * 64 * csz,
+        "spread_reduce": n_items * 64 * csz + band,
         "band_inv": band + Bc,
         "row_inv": A + Bc + 8 * n * n,
     }[stage])
@@ -304,6 +306,7 @@ def run_ours(args):
     tw1 = time.time()
     ms_total = e0.elapsed_time(e1)
     stage_ms, n_prof = plan.profile_end()
+    n_stages = len(stage_ms)
     clk = clocks.summary(tw0, tw1)
     clocks.stop()
     t_max = max_over_ranks(ms_total / 1000.0)
@@ -358,7 +361,8 @@ def run_ours(args):
     avg = {k: v / max(1, n_prof) for k, v in stage_ms.items()}
     dom = max(avg, key=avg.get)
     peak, peak_src = load_peaks()
-    alg = algorithmic_bytes(dom, n, info.band_q, csz, info.n_nodes, info.kernel_width, rsz)
+    alg = algorithmic_bytes(dom, n, info.band_q, csz, info.n_nodes, info.kernel_width, rsz,
+                            info.n_items)
     achieved = alg / (avg[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
@@ -381,7 +385,7 @@ def run_ours(args):
                  "dtype": "f64", "mixed_speedup": value / value64},
         "roofline": roofline,
         "e2e": e2e,
-        "gpu_launches": args.steps * 7,
+        "gpu_launches": args.steps * n_stages,
         "clocks": clk,
     }
 

@@ -189,6 +189,8 @@ typedef struct {
   double  es_beta;       /* ES shape parameter */
   int32_t n_tiles;       /* spreading tiles */
   int32_t max_tile_nodes;
+  int32_t n_items;       /* spreading work items (tiles cut into pieces) */
+  int32_t reserved;
 } dsnu_plan_info;
 
 dsnu_status dsnu_plan_get_info(dsnu_plan plan, dsnu_plan_info* info);

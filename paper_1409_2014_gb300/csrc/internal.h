@@ -28,22 +28,20 @@ struct PlanTables {
   int2* node_q0;  // n_nodes
   void* node_w;   // real, n_nodes * 2w (x weights then y weights)
   double* node_D; // n_nodes
-  int* tile_ptr;  // n_tiles + 1: spreading tile -> entry range
+  int* tile_items;  // n_tiles + 1: spreading tile -> range of work items
+  int2* item_range; // per work item: [first, end) entry
+  int* item_tile;   // per work item: its tile
   int* ent_node;  // per entry: node index
   int2* ent_q0;   // per entry: stencil origin of the node
   void* ent_w;    // real, per entry: the node's 2w ES weights
   int* status;    // one int
 };
 
-// Side stream and fork/join events owned by a plan.
-struct StreamSet {
-  cudaStream_t side;
-  cudaEvent_t fork, join;
-};
+
 
 // Workspace layout (offsets in bytes from the workspace base).
 struct WsLayout {
-  size_t off_A, off_B, off_Bband, off_Sband, off_c, total;
+  size_t off_A, off_B, off_Bband, off_Sband, off_c, off_partial, total;
   int ldqA, ldqB, ldq;  // q columns of the row-tiled A and B; band column length
 };
 
@@ -53,23 +51,23 @@ struct PlanGeom {
   int n_gy;                // entries of the short partition table
   double dky2;             // dk_y^2
   int grid_rowf, grid_col, grid_bandf, grid_bandi, grid_rowi;  // persistent grid sizes
-  int w, Q, n_nodes, n_tiles, tiles_x, tiles_y, max_tile_nodes;
+  int w, Q, n_nodes, n_tiles, tiles_x, tiles_y, max_tile_nodes, n_items;
   int precision, sharp;
   double beta, sigma, cut_radius;
   double scale;  // 1/(Mx My)
 };
 
-constexpr int kStages = 7;       // kernels per solve
-constexpr int kProfEvents = 9;   // events per profiled solve (see run_pipeline)
+constexpr int kStages = 8;       // kernels per solve
+constexpr int kProfEvents = kStages + 1;  // events per profiled solve (see run_pipeline)
 
 // Launchers (one translation unit per precision).  `ev`, when not NULL,
 // holds kProfEvents events recorded around the kernels.
 dsnu_status run_pipeline_f32(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
                              const double* rho, double* phi, cudaStream_t st, int cj,
-                             const StreamSet& ss, cudaEvent_t* ev);
+                             cudaEvent_t* ev);
 dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
                              const double* rho, double* phi, cudaStream_t st, int cj,
-                             const StreamSet& ss, cudaEvent_t* ev);
+                             cudaEvent_t* ev);
 // Set the kernels' shared-memory limits and compute persistent grid sizes.
 cudaError_t prepare_kernels_f32(PlanGeom& g);
 cudaError_t prepare_kernels_f64(PlanGeom& g);
@@ -87,7 +85,6 @@ struct dsnu_plan_s {
   size_t table_bytes;
   void* ws;                 // caller-owned workspace
   size_t ws_bytes;
-  dsnu::StreamSet streams;  // side stream for the band chain
   cudaEvent_t* prof_events; // profiling: max_solves * kProfEvents events, or NULL
   int prof_max, prof_used;
 };

@@ -73,6 +73,7 @@ struct MultTabs {
   const R* gx;        // 1 - exp(-(q_x dk_x)^2 / sigma^2)
   int n_gy;           // 1 - exp(-(a dk_y)^2 / sigma^2) rounds to 1 for a = |qbar_y| >= n_gy
   R inv_sigma2;       // 1 / sigma^2
+  R neg_dky2_s2_log2e;  // -dk_y^2 / (sigma^2 ln 2)
   R dky2;             // dk_y^2
   int half_my;        // N_y (= M_y / 2)
   int sharp;          // 1: p = indicator of |k| <= P
@@ -92,6 +93,11 @@ __device__ __forceinline__ R mult_high(const MultTabs<R>& mt, R wx2, R gx, int q
   R part;
   if (mt.sharp) {
     part = (s > mt.cut2) ? R(1) : R(0);
+  } else if constexpr (sizeof(R) == 4) {
+    // 1 - e^{-kx^2/s^2} e^{-ky^2/s^2} with e^{-ky^2/s^2} = 2^{-a^2 dk^2 / (s^2 ln 2)}
+    // (hardware exp2): absolute error ~1e-7, at the level of FP32 rounding of m1
+    const R ey = exp2f(R(a * a) * mt.neg_dky2_s2_log2e);
+    part = R(1) - (R(1) - gx) * ey;
   } else {
     // 1 - exp(-ky^2/s^2): below working precision of 1 only for a < n_gy
     const R gy = (a < mt.n_gy) ? -expm1_r(-wy2 * mt.inv_sigma2) : R(1);
@@ -134,7 +140,7 @@ struct Geo {
   static constexpr int T_RF = (RB_F * G > 512) ? 512 : RB_F * G;
   static constexpr int RPG_F = RB_F / (T_RF / G);
   // inverse row pass: RB_I rows per CTA, one group per row
-  static constexpr int RB_I0 = (sizeof(R) == 4) ? ((2 * G >= 256) ? 2 : 256 / G)
+  static constexpr int RB_I0 = (sizeof(R) == 4) ? ((TR * G >= 256) ? TR : 256 / G)
                                                 : ((G >= 256) ? 1 : 256 / G);
   static constexpr int RB_I = (RB_I0 < RMAX / 2) ? RB_I0 : RMAX / 2;
   static constexpr int T_RI = RB_I * G;
@@ -375,48 +381,85 @@ k_interp(const cpx<R>* __restrict__ Bband, int ldq, int Q, const int2* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Type-1 spreading as a gather: one CTA per 8 x 8 tile of band cells; the
-// (node, stencil origin, ES weights) entries of every node whose stencil meets
-// the tile are laid out contiguously per tile at plan time, so a chunk of 64
-// entries is fetched with independent loads.
+// Type-1 spreading as a gather over 8 x 8 tiles of band cells.  At plan time
+// the (node, stencil origin, ES weights) entries of every node whose stencil
+// meets a tile are laid out contiguously per tile and cut into work items of
+// at most kSpreadChunk entries.  k_spread: one CTA per work item; each cell is
+// served by kSplit threads that take every kSplit-th entry; the CTA writes the
+// item's partial sums.  k_spread_reduce: per tile, adds its items' partial
+// sums in item order (deterministic, no atomics) and applies the centring
+// phase.
 constexpr int kTile = 8;
-constexpr int kSpreadChunk = 64;
+constexpr int kSplit = 4;
+constexpr int kSpreadThreads = kTile * kTile * kSplit;
+constexpr int kSpreadChunk = 128;
+
+template <typename R>
+__global__ void __launch_bounds__(kSpreadThreads)
+k_spread(const cpx<R>* __restrict__ c, const int2* __restrict__ item_range,
+         const int* __restrict__ ent_node, const int2* __restrict__ ent_q0,
+         const R* __restrict__ ent_w, const int* __restrict__ item_tile, int w, int tiles_x, int Q,
+         cpx<R>* __restrict__ partial) {
+  __shared__ int2 s_q0[kSpreadChunk];
+  __shared__ cpx<R> s_c[kSpreadChunk];
+  __shared__ R s_w[kSpreadChunk * 32];
+  __shared__ R s_red[2][kSplit][kTile * kTile];
+  const int item = blockIdx.x;
+  const int tile = item_tile[item];
+  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  const int cell = threadIdx.x & (kTile * kTile - 1), part = threadIdx.x / (kTile * kTile);
+  const int qx = tx * kTile + (cell & (kTile - 1));
+  const int qy = ty * kTile + (cell / kTile) - Q;
+  const int2 rg = item_range[item];
+  const int s0 = rg.x, cnt = rg.y - rg.x;  // cnt <= kSpreadChunk
+  const int w2 = 2 * w;
+  for (int i = threadIdx.x; i < cnt; i += kSpreadThreads) {
+    s_q0[i] = ent_q0[s0 + i];
+    s_c[i] = c[ent_node[s0 + i]];
+  }
+  const R* src = ent_w + size_t(s0) * w2;
+  for (int i = threadIdx.x; i < cnt * w2; i += kSpreadThreads) {
+    const int e = i / w2;
+    s_w[e * 32 + (i - e * w2)] = src[i];
+  }
+  __syncthreads();
+  R ax = R(0), ay = R(0);
+  for (int k = part; k < cnt; k += kSplit) {
+    const int a = qx - s_q0[k].x, b = qy - s_q0[k].y;
+    if ((unsigned)a < (unsigned)w && (unsigned)b < (unsigned)w) {
+      const R f = s_w[k * 32 + a] * s_w[k * 32 + w + b];
+      ax += f * s_c[k].x;
+      ay += f * s_c[k].y;
+    }
+  }
+  s_red[0][part][cell] = ax;
+  s_red[1][part][cell] = ay;
+  __syncthreads();
+  if (part == 0) {
+#pragma unroll
+    for (int p = 1; p < kSplit; ++p) {
+      ax += s_red[0][p][cell];
+      ay += s_red[1][p][cell];
+    }
+    partial[size_t(item) * (kTile * kTile) + cell] = mk<R>(ax, ay);
+  }
+}
 
 template <typename R>
 __global__ void __launch_bounds__(kTile * kTile)
-k_spread(const cpx<R>* __restrict__ c, const int* __restrict__ tile_ptr,
-         const int* __restrict__ ent_node, const int2* __restrict__ ent_q0,
-         const R* __restrict__ ent_w, int w, int tiles_x, int Q, cpx<R>* __restrict__ Sband,
-         int ldq, int cj) {
-  __shared__ int2 s_q0[kSpreadChunk];
-  __shared__ cpx<R> s_c[kSpreadChunk];
-  __shared__ R s_w[kSpreadChunk][33];
+k_spread_reduce(const cpx<R>* __restrict__ partial, const int* __restrict__ tile_items, int tiles_x,
+                int n_tiles, int Q, cpx<R>* __restrict__ Sband, int ldq, int cj) {
   const int tile = blockIdx.x;
+  if (tile >= n_tiles) return;
+  const int cell = threadIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
-  const int qx = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int qy = ty * kTile + (threadIdx.x / kTile) - Q;
+  const int qx = tx * kTile + (cell & (kTile - 1));
+  const int qy = ty * kTile + (cell / kTile) - Q;
   R ax = R(0), ay = R(0);
-  const int beg = tile_ptr[tile], end = tile_ptr[tile + 1];
-  const int w2 = 2 * w;
-  for (int s0 = beg; s0 < end; s0 += kSpreadChunk) {
-    const int cnt = min(kSpreadChunk, end - s0);
-    const int i = threadIdx.x;
-    if (i < cnt) {
-      s_q0[i] = ent_q0[s0 + i];
-      s_c[i] = c[ent_node[s0 + i]];
-      const R* src = ent_w + size_t(s0 + i) * w2;
-      for (int a = 0; a < w2; ++a) s_w[i][a] = src[a];
-    }
-    __syncthreads();
-    for (int k = 0; k < cnt; ++k) {
-      const int a = qx - s_q0[k].x, b = qy - s_q0[k].y;
-      if ((unsigned)a < (unsigned)w && (unsigned)b < (unsigned)w) {
-        const R f = s_w[k][a] * s_w[k][w + b];
-        ax += f * s_c[k].x;
-        ay += f * s_c[k].y;
-      }
-    }
-    __syncthreads();
+  for (int it = tile_items[tile]; it < tile_items[tile + 1]; ++it) {
+    const cpx<R> v = partial[size_t(it) * (kTile * kTile) + cell];
+    ax += v.x;
+    ay += v.y;
   }
   if (qx <= Q && qy <= Q) {
     const int e = qx + qy;
@@ -476,7 +519,7 @@ k_band_inv(const cpx<R>* __restrict__ Sband, int ldq, int Q, int ncols, cpx<R>* 
 //   T(2j+1) = IDFT_N[(W(q) - W(q + N)) e^{+2 pi i q/M}](j),   q < N,
 // with W(q) = Y(q) + i S(q) for q <= N and W(M - q) = conj Y(q) + i conj S(q).
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(DSNU_ROW_MINB))
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(Geo<R, LOG2N>::T_RI > 512 ? 1 : DSNU_ROW_MINB))
 k_row_inv(const cpx<R>* __restrict__ A, int ldqA, const cpx<R>* __restrict__ St, int ldqB, int Q,
           double* __restrict__ phi, int ny, AxisTabs<R> ax, const R* __restrict__ decon_y, R scale,
           int cj) {

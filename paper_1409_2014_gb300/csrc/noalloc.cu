@@ -95,9 +95,9 @@ dsnu_status dsnu_solve_noalloc(dsnu_plan plan, const double* rho, double* phi, v
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (plan->geom.precision == DSNU_MIXED)
     return dsnu::run_pipeline_f32(plan->geom, plan->tab, plan->ws_layout, scratch, rho, phi, st, 0,
-                                  plan->streams, nullptr);
+                                  nullptr);
   return dsnu::run_pipeline_f64(plan->geom, plan->tab, plan->ws_layout, scratch, rho, phi, st, 0,
-                                plan->streams, nullptr);
+                                nullptr);
 }
 
 }  // extern "C"

@@ -79,15 +79,13 @@ cudaError_t prepare_kernels(PlanGeom& g) {
   return e;
 }
 
-// One solve.  row_fwd runs on `st`; the band chain (band_fwd, interp, spread,
-// band_inv) runs on the plan's side stream concurrently with col_main, and
-// row_inv waits for both.  With `ev` (profiling) the kStages + 2 events are:
-// 0 before row_fwd, 1 after row_fwd (fork), 2 after col_main, 3..6 after the
-// four band kernels (side stream), 7 after the join on `st`, 8 after row_inv.
+// One solve, all kernels in order on `st`: row_fwd, the band chain
+// (band_fwd, interp, spread, spread_reduce, band_inv), col_main, row_inv.  With `ev`
+// (profiling) kProfEvents events are recorded before the first kernel and
+// after each kernel, in launch order.
 template <typename R>
 dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
-                         const double* rho, double* phi, cudaStream_t st, int cj,
-                         const StreamSet& ss, cudaEvent_t* ev) {
+                         const double* rho, double* phi, cudaStream_t st, int cj, cudaEvent_t* ev) {
   char* base = static_cast<char*>(ws);
   cpx<R>* A = reinterpret_cast<cpx<R>*>(base + L.off_A);
   cpx<R>* B = reinterpret_cast<cpx<R>*>(base + L.off_B);
@@ -99,12 +97,12 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
   const AxisTabs<R> ay{static_cast<const cpx<R>*>(t.stw_y), static_cast<const cpx<R>*>(t.twm_lo_y),
                        static_cast<const cpx<R>*>(t.twm_hi_y), g.log2lo_y, static_cast<const R*>(t.decon_y)};
   const MultTabs<R> mt{static_cast<const R*>(t.m_wx2), static_cast<const R*>(t.m_gx),
-                       g.n_gy, R(1.0 / (g.sigma * g.sigma)), R(g.dky2), g.ny, g.sharp,
+                       g.n_gy, R(1.0 / (g.sigma * g.sigma)),
+                       R(-g.dky2 / (g.sigma * g.sigma) * 1.4426950408889634), R(g.dky2), g.ny, g.sharp,
                        R(g.cut_radius * g.cut_radius)};
   const R* dcy = static_cast<const R*>(t.decon_y);
   const R* wts = static_cast<const R*>(t.node_w);
   const int ldqA = L.ldqA, ldqB = L.ldqB;
-  cudaStream_t sd = ss.side;
 
 #define DSNU_ROWF(L2)                                                                               \
   k_row_fwd<R, L2><<<g.grid_rowf, Geo<R, L2>::T_RF,                                               \
@@ -114,53 +112,54 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
                       Geo<R, L2>::smem_col, st>>>(A, ldqA, g.nx + 1, ay, mt, cj)
 #define DSNU_BANDF(L2)                                                                                \
   k_band_fwd<R, L2><<<g.grid_bandf, Geo<R, L2>::T_C,                                               \
-                      Geo<R, L2>::smem_band_fwd, sd>>>(B, ldqB, g.Q + 1, Bband, L.ldq, g.Q, ay, cj)
+                      Geo<R, L2>::smem_band_fwd, st>>>(B, ldqB, g.Q + 1, Bband, L.ldq, g.Q, ay, cj)
 #define DSNU_BANDI(L2)                                                                                \
   k_band_inv<R, L2><<<g.grid_bandi, Geo<R, L2>::T_C,                                               \
-                      Geo<R, L2>::smem_col, sd>>>(Sband, L.ldq, g.Q, g.Q + 1, B, ldqB, ay, cj)
+                      Geo<R, L2>::smem_col, st>>>(Sband, L.ldq, g.Q, g.Q + 1, B, ldqB, ay, cj)
 #define DSNU_ROWI(L2)                                                                                 \
   k_row_inv<R, L2><<<g.grid_rowi, Geo<R, L2>::T_RI,                                                \
                      Geo<R, L2>::smem_row_inv, st>>>(A, ldqA, B, ldqB, g.Q, phi, g.ny, ax, dcy,     \
                                                      R(g.scale), cj)
-#define DSNU_MARK(I, S) \
-  if (ev) cudaEventRecord(ev[I], S)
-  DSNU_MARK(0, st);
+#define DSNU_MARK(I) \
+  if (ev) cudaEventRecord(ev[I], st)
+  DSNU_MARK(0);
   switch (g.log2nx) {
     DSNU_LOG2_CASES(DSNU_ROWF)
     default: return DSNU_EUNSUPPORTED;
   }
-  cudaEventRecord(ev ? ev[1] : ss.fork, st);
-  cudaStreamWaitEvent(sd, ev ? ev[1] : ss.fork, 0);
-  switch (g.log2ny) {
-    DSNU_LOG2_CASES(DSNU_COLM)
-    default: return DSNU_EUNSUPPORTED;
-  }
-  DSNU_MARK(2, st);
+  DSNU_MARK(1);
   switch (g.log2ny) {
     DSNU_LOG2_CASES(DSNU_BANDF)
     default: return DSNU_EUNSUPPORTED;
   }
-  DSNU_MARK(3, sd);
-  k_interp<R><<<(g.n_nodes + 7) / 8, 256, 0, sd>>>(Bband, L.ldq, g.Q, t.node_q0, wts, t.node_D,
+  DSNU_MARK(2);
+  k_interp<R><<<(g.n_nodes + 7) / 8, 256, 0, st>>>(Bband, L.ldq, g.Q, t.node_q0, wts, t.node_D,
                                                    g.n_nodes, g.w, cn, cj);
-  DSNU_MARK(4, sd);
-  k_spread<R><<<g.n_tiles, kTile * kTile, 0, sd>>>(cn, t.tile_ptr, t.ent_node, t.ent_q0,
-                                                   static_cast<const R*>(t.ent_w), g.w, g.tiles_x,
-                                                   g.Q, Sband, L.ldq, cj);
-  DSNU_MARK(5, sd);
+  DSNU_MARK(3);
+  cpx<R>* partial = reinterpret_cast<cpx<R>*>(base + L.off_partial);
+  if (g.n_items > 0)
+    k_spread<R><<<g.n_items, kSpreadThreads, 0, st>>>(cn, t.item_range, t.ent_node, t.ent_q0,
+                                                      static_cast<const R*>(t.ent_w), t.item_tile, g.w,
+                                                      g.tiles_x, g.Q, partial);
+  DSNU_MARK(4);
+  k_spread_reduce<R><<<g.n_tiles, kTile * kTile, 0, st>>>(partial, t.tile_items, g.tiles_x, g.n_tiles,
+                                                         g.Q, Sband, L.ldq, cj);
+  DSNU_MARK(5);
   switch (g.log2ny) {
     DSNU_LOG2_CASES(DSNU_BANDI)
     default: return DSNU_EUNSUPPORTED;
   }
-  DSNU_MARK(6, sd);
-  cudaEventRecord(ss.join, sd);
-  cudaStreamWaitEvent(st, ss.join, 0);
-  DSNU_MARK(7, st);
+  DSNU_MARK(6);
+  switch (g.log2ny) {
+    DSNU_LOG2_CASES(DSNU_COLM)
+    default: return DSNU_EUNSUPPORTED;
+  }
+  DSNU_MARK(7);
   switch (g.log2nx) {
     DSNU_LOG2_CASES(DSNU_ROWI)
     default: return DSNU_EUNSUPPORTED;
   }
-  DSNU_MARK(8, st);
+  DSNU_MARK(8);
 #undef DSNU_ROWF
 #undef DSNU_COLM
 #undef DSNU_BANDF

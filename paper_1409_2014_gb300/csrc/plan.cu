@@ -24,8 +24,8 @@
 #include <string>
 #include <vector>
 
-#include "common.cuh"
 #include "internal.h"
+#include "kernels.cuh"
 
 namespace dsnu {
 
@@ -120,7 +120,8 @@ struct HostTables {
   std::vector<int2> node_q0;
   std::vector<R> node_w;
   std::vector<double> node_D;
-  std::vector<int> tile_ptr, ent_node;
+  std::vector<int> tile_ptr, ent_node, tile_items, item_tile;
+  std::vector<int2> item_range;
   std::vector<int2> ent_q0;
   std::vector<R> ent_w;
 };
@@ -279,7 +280,7 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
 
   // spreading tiles (kTile x kTile cells) over q_x in [0, Q], q_y in [-Q, Q];
   // per tile, the entries of every node whose stencil meets it
-  const int TS = 8;
+  const int TS = kTile;
   g.tiles_x = (Q + 1 + TS - 1) / TS;
   g.tiles_y = (2 * Q + 1 + TS - 1) / TS;
   g.n_tiles = g.tiles_x * g.tiles_y;
@@ -313,6 +314,20 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
     T.ent_q0.push_back(make_int2(0, 0));
     T.ent_w.resize(2 * w, R(0));
   }
+  // work items: each tile's entries cut into pieces of at most kSpreadChunk
+  T.tile_items.assign(g.n_tiles + 1, 0);
+  for (int i = 0; i < g.n_tiles; ++i) {
+    for (int b = T.tile_ptr[i]; b < T.tile_ptr[i + 1]; b += kSpreadChunk) {
+      T.item_range.push_back(make_int2(b, std::min(b + kSpreadChunk, T.tile_ptr[i + 1])));
+      T.item_tile.push_back(i);
+    }
+    T.tile_items[i + 1] = int(T.item_range.size());
+  }
+  g.n_items = int(T.item_range.size());
+  if (T.item_range.empty()) {
+    T.item_range.push_back(make_int2(0, 0));
+    T.item_tile.push_back(0);
+  }
 
   // one device block for every table
   Builder b;
@@ -322,7 +337,8 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   const size_t o_dy = b.add(T.decon_y);
   const size_t o_wx2 = b.add(T.m_wx2), o_gx = b.add(T.m_gx), o_gy = b.add(T.m_gy);
   const size_t o_q0 = b.add(T.node_q0), o_w = b.add(T.node_w), o_D = b.add(T.node_D);
-  const size_t o_tp = b.add(T.tile_ptr), o_en = b.add(T.ent_node), o_eq = b.add(T.ent_q0);
+  const size_t o_ti = b.add(T.tile_items), o_ir = b.add(T.item_range), o_it = b.add(T.item_tile);
+  const size_t o_en = b.add(T.ent_node), o_eq = b.add(T.ent_q0);
   const size_t o_ew = b.add(T.ent_w);
   const int zero = 0;
   const size_t o_st = b.add(&zero, sizeof(int));
@@ -343,7 +359,9 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   t.node_q0 = reinterpret_cast<int2*>(d + o_q0);
   t.node_w = d + o_w;
   t.node_D = reinterpret_cast<double*>(d + o_D);
-  t.tile_ptr = reinterpret_cast<int*>(d + o_tp);
+  t.tile_items = reinterpret_cast<int*>(d + o_ti);
+  t.item_range = reinterpret_cast<int2*>(d + o_ir);
+  t.item_tile = reinterpret_cast<int*>(d + o_it);
   t.ent_node = reinterpret_cast<int*>(d + o_en);
   t.ent_q0 = reinterpret_cast<int2*>(d + o_eq);
   t.ent_w = d + o_ew;
@@ -371,6 +389,7 @@ static void layout_workspace(dsnu_plan_s* P) {
   L.off_Bband = take(size_t(g.Q + 1) * L.ldq * csz);
   L.off_Sband = take(size_t(g.Q + 1) * L.ldq * csz);
   L.off_c = take(size_t(g.n_nodes) * csz);
+  L.off_partial = take(size_t(std::max(g.n_items, 1)) * kTile * kTile * csz);
   L.total = off;
 }
 
@@ -434,14 +453,6 @@ dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan*
     return fail(DSNU_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
   }
   layout_workspace(P);
-  cudaError_t se = cudaStreamCreateWithFlags(&P->streams.side, cudaStreamNonBlocking);
-  if (se == cudaSuccess) se = cudaEventCreateWithFlags(&P->streams.fork, cudaEventDisableTiming);
-  if (se == cudaSuccess) se = cudaEventCreateWithFlags(&P->streams.join, cudaEventDisableTiming);
-  if (se != cudaSuccess) {
-    cudaFree(P->table_block);
-    delete P;
-    return fail(DSNU_ECUDA, std::string("stream/event creation: ") + cudaGetErrorString(se));
-  }
   *out = P;
   return DSNU_OK;
 }
@@ -470,10 +481,8 @@ static dsnu_status run(dsnu_plan plan, const double* in, double* out, void* stre
   if (plan->prof_events && plan->prof_used < plan->prof_max)
     ev = plan->prof_events + size_t(plan->prof_used++) * kProfEvents;
   if (plan->geom.precision == DSNU_MIXED)
-    return run_pipeline_f32(plan->geom, plan->tab, plan->ws_layout, plan->ws, in, out, st, cj,
-                            plan->streams, ev);
-  return run_pipeline_f64(plan->geom, plan->tab, plan->ws_layout, plan->ws, in, out, st, cj,
-                          plan->streams, ev);
+    return run_pipeline_f32(plan->geom, plan->tab, plan->ws_layout, plan->ws, in, out, st, cj, ev);
+  return run_pipeline_f64(plan->geom, plan->tab, plan->ws_layout, plan->ws, in, out, st, cj, ev);
 }
 
 static void free_profile(dsnu_plan plan) {
@@ -506,10 +515,6 @@ dsnu_status dsnu_status_poll(dsnu_plan plan, void* stream) {
 dsnu_status dsnu_plan_destroy(dsnu_plan plan) {
   if (!plan) return DSNU_OK;
   free_profile(plan);
-  cudaStreamSynchronize(plan->streams.side);
-  cudaEventDestroy(plan->streams.fork);
-  cudaEventDestroy(plan->streams.join);
-  cudaStreamDestroy(plan->streams.side);
   cudaError_t e = cudaFree(plan->table_block);
   delete plan;
   if (e != cudaSuccess) return fail(DSNU_ECUDA, std::string("cudaFree: ") + cudaGetErrorString(e));
@@ -557,14 +562,13 @@ dsnu_status dsnu_profile_end(dsnu_plan plan, double* stage_ms, int n_stages, int
   for (int k = 0; k < kStages; ++k) stage_ms[k] = 0.0;
   dsnu_status st = DSNU_OK;
   // stage k runs between events (from[k], to[k]) of a solve (see run_pipeline)
-  static const int from[kStages] = {0, 1, 1, 3, 4, 5, 7};
-  static const int to[kStages] = {1, 2, 3, 4, 5, 6, 8};
+  // stage k runs between events k and k + 1 (launch order)
   for (int s = 0; s < plan->prof_used && st == DSNU_OK; ++s) {
     cudaEvent_t* ev = plan->prof_events + size_t(s) * kProfEvents;
     cudaError_t e = cudaEventSynchronize(ev[kProfEvents - 1]);
     for (int k = 0; k < kStages && e == cudaSuccess; ++k) {
       float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, ev[from[k]], ev[to[k]]);
+      e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
       stage_ms[k] += ms;
     }
     if (e != cudaSuccess) st = fail(DSNU_ECUDA, std::string("profile events: ") + cudaGetErrorString(e));
@@ -577,8 +581,8 @@ dsnu_status dsnu_profile_end(dsnu_plan plan, double* stage_ms, int n_stages, int
 int32_t dsnu_stage_count(void) { return kStages; }
 
 const char* dsnu_stage_name(int32_t stage) {
-  static const char* names[kStages] = {"row_fwd", "col_main", "band_fwd", "interp",
-                                       "spread", "band_inv", "row_inv"};
+  static const char* names[kStages] = {"row_fwd", "band_fwd", "interp", "spread",
+                                       "spread_reduce", "band_inv", "col_main", "row_inv"};
   return (stage >= 0 && stage < kStages) ? names[stage] : "";
 }
 
@@ -593,6 +597,8 @@ dsnu_status dsnu_plan_get_info(dsnu_plan plan, dsnu_plan_info* info) {
   info->es_beta = g.beta;
   info->n_tiles = g.n_tiles;
   info->max_tile_nodes = g.max_tile_nodes;
+  info->n_items = g.n_items;
+  info->reserved = 0;
   return DSNU_OK;
 }
 

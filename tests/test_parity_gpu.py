@@ -186,6 +186,6 @@ def test_profile_reports_every_stage():
     for _ in range(5):
         plan.solve(rho)
     stages, cnt = plan.profile_end()
-    assert cnt == 3 and len(stages) == dsnu_stage_count() == 7
+    assert cnt == 3 and len(stages) == dsnu_stage_count() == 8
     assert all(v > 0 for v in stages.values())
     plan.close()
