@@ -179,6 +179,62 @@ dsnu_status dsnu_solve_noalloc(dsnu_plan plan, const double* rho_dev, double* ph
 /* Size in bytes of the static scratch used by dsnu_solve_noalloc. */
 size_t dsnu_noalloc_scratch_bytes(void);
 
+/* ---------------------------------------------------------------------------
+ * Split-step pieces of the DS time loop (Sec. 2.3, time-splitting spectral
+ * method).  A DS plan holds the unpadded N x N periodic transform of the wave
+ * function u on [-lx,lx) x [-ly,ly); u is interleaved complex [ny][nx]
+ * (complex64 when precision = DSNU_MIXED, complex128 when DSNU_FP64).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t nx, ny;    /* powers of two, 16..4096 */
+  double  lx, ly;    /* half-widths */
+  int32_t precision; /* dsnu_precision: DSNU_MIXED (complex64) or DSNU_FP64 (complex128) */
+  int32_t reserved;
+} dsnu_ds_params;
+
+typedef struct dsnu_ds_plan_s* dsnu_ds_plan;
+
+/* Build the transform tables (FP64 on the host, uploaded on `stream`, which is
+ * then synchronised).  Errors: DSNU_EINVAL, DSNU_ENOMEM, DSNU_ECUDA. */
+dsnu_status dsnu_ds_plan_create(const dsnu_ds_params* params, void* stream, dsnu_ds_plan* out);
+
+/* Load the phases of the linear flow over a step tau (eqs. 1st_tssp,
+ * 1st_tssp_more): e^{-i tau (k_x^2 - alpha k_y^2)}, k angular wave numbers of
+ * the periodic grid.  Generated in FP64 on the host and uploaded (synchronises
+ * `stream`) unless the same (tau, alpha) is already loaded. */
+dsnu_status dsnu_ds_set_linear_step(dsnu_ds_plan plan, double tau, double alpha, void* stream);
+
+/* u <- F^-1[ e^{-i tau (k_x^2 - alpha k_y^2)} F[u] ] in place (the exact
+ * linear flow); adjoint != 0 applies the conjugate phases, i.e. the inverse
+ * (= adjoint, the flow is unitary) propagator.  Errors: DSNU_EINVAL (no step
+ * loaded), DSNU_ECUDA. */
+dsnu_status dsnu_ds_linear(dsnu_ds_plan plan, void* u_dev, int32_t adjoint, void* stream);
+
+/* rho <- |u|^2 (FP64 [ny][nx], device), the density of eq. DSII_exact_pot. */
+dsnu_status dsnu_ds_abs2(dsnu_ds_plan plan, const void* u_dev, double* rho_dev, void* stream);
+
+/* Nonlinear flow with the density and Phi frozen over a step (eqs. 2nd_tssp,
+ * 2nd_tssp_more): u <- u e^{i tau (2 beta |u|^2 + 4 beta Phi)} in place;
+ * phi_dev: FP64 [ny][nx] potential of the current density. */
+dsnu_status dsnu_ds_nonlinear(dsnu_ds_plan plan, void* u_dev, const double* phi_dev, double tau,
+                              double beta, void* stream);
+
+/* Vector-Jacobian product of the nonlinear flow u' = u e^{i theta}, theta =
+ * tau (2 beta |u|^2 + 4 beta Phi(|u|^2)), for a real loss with gradients in
+ * the d/dRe + i d/dIm convention.  Given u (the step's input), Phi and g' (the
+ * gradient at u'), writes part = g' e^{-i theta} (complex, like u) and s =
+ * Im(g' conj u') (FP64); the caller forms A^T s with dsnu_solve_adjoint and
+ * calls dsnu_ds_nonlinear_vjp_finish, which turns part into
+ *   grad_u = part + 2 tau (2 beta s + 4 beta A^T s) u. */
+dsnu_status dsnu_ds_nonlinear_vjp(dsnu_ds_plan plan, const void* u_dev, const double* phi_dev,
+                                  const void* g_dev, double tau, double beta, double* s_dev,
+                                  void* part_dev, void* stream);
+dsnu_status dsnu_ds_nonlinear_vjp_finish(dsnu_ds_plan plan, const void* u_dev, const double* s_dev,
+                                         const double* ats_dev, double tau, double beta,
+                                         void* grad_dev, void* stream);
+
+dsnu_status dsnu_ds_plan_destroy(dsnu_ds_plan plan);
+
 /* Plan introspection for tests and benchmarks (host values, no device work). */
 typedef struct {
   int32_t n_nodes;       /* n_r * n_theta */

@@ -25,6 +25,8 @@ EXPORTED = [
     "dsnu_solve_adjoint", "dsnu_status_poll", "dsnu_plan_destroy", "dsnu_last_error",
     "dsnu_plan_get_info", "dsnu_solve_host", "dsnu_profile_begin", "dsnu_profile_end",
     "dsnu_stage_count", "dsnu_stage_name", "dsnu_solve_noalloc", "dsnu_noalloc_scratch_bytes",
+    "dsnu_ds_plan_create", "dsnu_ds_set_linear_step", "dsnu_ds_linear", "dsnu_ds_abs2",
+    "dsnu_ds_nonlinear", "dsnu_ds_nonlinear_vjp", "dsnu_ds_nonlinear_vjp_finish", "dsnu_ds_plan_destroy",
 ]
 
 
@@ -46,6 +48,14 @@ class dsnu_plan_info(ctypes.Structure):
         ("sigma", ctypes.c_double), ("es_beta", ctypes.c_double),
         ("n_tiles", ctypes.c_int32), ("max_tile_nodes", ctypes.c_int32),
         ("n_items", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class dsnu_ds_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -100,6 +110,19 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dsnu_solve_noalloc.restype = st
     lib.dsnu_noalloc_scratch_bytes.argtypes = []
     lib.dsnu_noalloc_scratch_bytes.restype = ctypes.c_size_t
+    d = ctypes.c_double
+    lib.dsnu_ds_plan_create.argtypes = [ctypes.POINTER(dsnu_ds_params), vp, ctypes.POINTER(vp)]
+    lib.dsnu_ds_set_linear_step.argtypes = [vp, d, d, vp]
+    lib.dsnu_ds_linear.argtypes = [vp, vp, ctypes.c_int32, vp]
+    lib.dsnu_ds_abs2.argtypes = [vp, vp, vp, vp]
+    lib.dsnu_ds_nonlinear.argtypes = [vp, vp, vp, d, d, vp]
+    lib.dsnu_ds_nonlinear_vjp.argtypes = [vp, vp, vp, vp, d, d, vp, vp, vp]
+    lib.dsnu_ds_nonlinear_vjp_finish.argtypes = [vp, vp, vp, vp, d, d, vp, vp]
+    lib.dsnu_ds_plan_destroy.argtypes = [vp]
+    for name in ("dsnu_ds_plan_create", "dsnu_ds_set_linear_step", "dsnu_ds_linear", "dsnu_ds_abs2",
+                 "dsnu_ds_nonlinear", "dsnu_ds_nonlinear_vjp", "dsnu_ds_nonlinear_vjp_finish",
+                 "dsnu_ds_plan_destroy"):
+        getattr(lib, name).restype = st
     _LIB = lib
     return lib
 
@@ -197,3 +220,47 @@ def dsnu_solve_noalloc(plan: int, rho_ptr: int, phi_ptr: int, stream: int = 0) -
 
 def dsnu_noalloc_scratch_bytes() -> int:
     return int(load().dsnu_noalloc_scratch_bytes())
+
+
+def _vp(x):
+    return ctypes.c_void_p(x)
+
+
+def dsnu_ds_plan_create(params: dsnu_ds_params, stream: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(load().dsnu_ds_plan_create(ctypes.byref(params), _vp(stream), ctypes.byref(out)),
+           "dsnu_ds_plan_create")
+    return out.value
+
+
+def dsnu_ds_set_linear_step(plan: int, tau: float, alpha: float, stream: int = 0) -> None:
+    _check(load().dsnu_ds_set_linear_step(_vp(plan), float(tau), float(alpha), _vp(stream)),
+           "dsnu_ds_set_linear_step")
+
+
+def dsnu_ds_linear(plan: int, u: int, adjoint: int, stream: int = 0) -> None:
+    _check(load().dsnu_ds_linear(_vp(plan), _vp(u), int(adjoint), _vp(stream)), "dsnu_ds_linear")
+
+
+def dsnu_ds_abs2(plan: int, u: int, rho: int, stream: int = 0) -> None:
+    _check(load().dsnu_ds_abs2(_vp(plan), _vp(u), _vp(rho), _vp(stream)), "dsnu_ds_abs2")
+
+
+def dsnu_ds_nonlinear(plan: int, u: int, phi: int, tau: float, beta: float, stream: int = 0) -> None:
+    _check(load().dsnu_ds_nonlinear(_vp(plan), _vp(u), _vp(phi), float(tau), float(beta), _vp(stream)),
+           "dsnu_ds_nonlinear")
+
+
+def dsnu_ds_nonlinear_vjp(plan, u, phi, g, tau, beta, s, part, stream=0) -> None:
+    _check(load().dsnu_ds_nonlinear_vjp(_vp(plan), _vp(u), _vp(phi), _vp(g), float(tau), float(beta),
+                                        _vp(s), _vp(part), _vp(stream)), "dsnu_ds_nonlinear_vjp")
+
+
+def dsnu_ds_nonlinear_vjp_finish(plan, u, s, ats, tau, beta, grad, stream=0) -> None:
+    _check(load().dsnu_ds_nonlinear_vjp_finish(_vp(plan), _vp(u), _vp(s), _vp(ats), float(tau),
+                                               float(beta), _vp(grad), _vp(stream)),
+           "dsnu_ds_nonlinear_vjp_finish")
+
+
+def dsnu_ds_plan_destroy(plan: int) -> None:
+    _check(load().dsnu_ds_plan_destroy(_vp(plan)), "dsnu_ds_plan_destroy")

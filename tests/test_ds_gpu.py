@@ -1,0 +1,192 @@
+"""GPU differentiation and split-step DS loop (through the C ABI) against the
+CPU oracle, finite differences and invariants."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import OracleParams
+from oracle import ds as D
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_2014_gb300.build import build
+
+    build()
+
+
+def _plans(n, L, prec, P=4.0, n_r=24, n_theta=48, sigma=2 / 3):
+    from paper_1409_2014_gb300 import Plan
+    from paper_1409_2014_gb300.ds import DSPlan
+
+    solver = Plan(n, lx=L, cut_radius=P, n_r=n_r, n_theta=n_theta, sigma=sigma, precision=prec)
+    ds = DSPlan(n, lx=L, precision=prec)
+    return solver, ds
+
+
+TOL = {"fp64": 1e-12, "mixed": 2e-5}
+CDT = {"fp64": torch.complex128, "mixed": torch.complex64}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_flows_match_oracle(prec):
+    n, L, tau, alpha, beta = 64, 8.0, 0.01, 1.0, 1.0
+    solver, ds = _plans(n, L, prec)
+    u_np = synth.wavefunction_sum(n, n, L, L, seed=4, count=3)
+    u = torch.from_numpy(u_np).to(CDT[prec]).cuda()
+    ds.set_linear_step(tau, alpha)
+    lin = ds.linear_(u.clone()).cpu().numpy()
+    ref = D.linear_flow(u_np, L, L, tau, alpha)
+    assert np.abs(lin - ref).max() <= TOL[prec] * np.abs(ref).max()
+    back = ds.linear_(torch.from_numpy(lin).to(CDT[prec]).cuda(), adjoint=True).cpu().numpy()
+    assert np.abs(back - u_np).max() <= 10 * TOL[prec] * np.abs(u_np).max()
+    rho = ds.abs2(u)
+    assert np.abs(rho.cpu().numpy() - np.abs(u_np) ** 2).max() <= TOL[prec] * np.abs(u_np).max() ** 2
+    phi = solver.solve(rho)
+    nl = ds.nonlinear_(u.clone(), phi, tau, beta).cpu().numpy()
+    ref_nl = D.nonlinear_flow(u_np, phi.cpu().numpy(), tau, beta)
+    assert np.abs(nl - ref_nl).max() <= TOL[prec] * np.abs(u_np).max()
+    solver.close()
+    ds.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_strang_steps_match_oracle(prec):
+    from paper_1409_2014_gb300.ds import evolve
+
+    n, L, tau = 64, 8.0, 0.01
+    solver, ds = _plans(n, L, prec)
+    p = OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=4.0, sigma=2 / 3, n_r=24, n_theta=48)
+    u_np = synth.wavefunction_sum(n, n, L, L, seed=4, count=3)
+    ref = u_np.copy()
+    for _ in range(3):
+        ref = D.strang_step(ref, p, tau, 1.0, 1.0)
+    with torch.no_grad():
+        out = evolve(torch.from_numpy(u_np).to(CDT[prec]).cuda(), 3, ds, solver, tau, 1.0, 1.0)
+    out = out.cpu().numpy()
+    assert np.abs(out - ref).max() <= 3 * TOL[prec] * np.abs(ref).max()
+    solver.close()
+    ds.close()
+
+
+def _loss_grad(u, w, solver):
+    from paper_1409_2014_gb300.ds import potential
+
+    u = u.detach().clone().requires_grad_(True)
+    rho = (u.real ** 2 + u.imag ** 2).to(torch.float64)
+    loss = (w * potential(rho, solver)).sum()
+    loss.backward()
+    return float(loss.detach()), u.grad
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_potential_gradient_matches_oracle_transpose(prec):
+    """dL/du for L = sum w Phi(|u|^2) equals 2 (A^T w) u (oracle's transposed sums)."""
+    n, L = 128, 16.0
+    solver, ds = _plans(n, L, prec, P=4.0, n_r=32, n_theta=64)
+    u_np = synth.wavefunction_sum(n, n, L, L, seed=4, count=6)
+    w_np = synth.normal_field(n, n, seed=44)
+    _, g = _loss_grad(torch.from_numpy(u_np).to(CDT[prec]).cuda(), torch.from_numpy(w_np).cuda(), solver)
+    p = OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=4.0, n_r=32, n_theta=64)
+    ref = 2.0 * oracle.solve_adjoint(w_np, p) * u_np
+    g = g.cpu().numpy()
+    assert np.abs(g - ref).max() <= 5 * TOL[prec] * np.abs(ref).max()
+    solver.close()
+    ds.close()
+
+
+def test_potential_gradient_central_differences_1024():
+    """complex128 u on 1024^2: directional derivatives vs central differences (h = 1e-6)."""
+    n, L = 1024, 32.0
+    solver, ds = _plans(n, L, "fp64", P=8.0, n_r=64, n_theta=256, sigma=0.0)
+    u = torch.from_numpy(synth.wavefunction_sum(n, n, L, L, seed=3, count=16)).cuda()
+    w = torch.from_numpy(synth.normal_field(n, n, seed=4)).cuda()
+    _, g = _loss_grad(u, w, solver)
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    from paper_1409_2014_gb300.ds import potential
+
+    def L_of(v):
+        with torch.no_grad():
+            return float((w * potential((v.real ** 2 + v.imag ** 2), solver)).sum())
+
+    h = 1e-6
+    for _ in range(4):
+        d = torch.complex(torch.randn(n, n, generator=gen, dtype=torch.float64),
+                          torch.randn(n, n, generator=gen, dtype=torch.float64)).cuda()
+        fd = (L_of(u + h * d) - L_of(u - h * d)) / (2 * h)
+        an = float((g.real * d.real + g.imag * d.imag).sum())
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3)
+    solver.close()
+    ds.close()
+
+
+def test_ds_loop_200_steps_checkpointed_gradient():
+    """1024^2 complex128, 200 Strang steps (alpha = 1, beta = 1, dt = 1e-3): mass
+    is conserved, and the gradient through checkpointed recomputation equals the
+    full-tape gradient and a central difference."""
+    from paper_1409_2014_gb300.ds import evolve, mass
+
+    n, L, tau, steps = 1024, 32.0, 1e-3, 200
+    solver, ds = _plans(n, L, "fp64", P=8.0, n_r=64, n_theta=256, sigma=0.0)
+    u0 = torch.from_numpy(synth.wavefunction_sum(n, n, L, L, seed=3, count=16)).cuda()
+    w = torch.from_numpy(synth.normal_field(n, n, seed=4)).cuda()
+
+    def loss_of(u):
+        return (w * (u.real ** 2 + u.imag ** 2)).sum()
+
+    grads = []
+    for ck in (14, 0):
+        u = u0.clone().requires_grad_(True)
+        out = evolve(u, steps, ds, solver, tau, 1.0, 1.0, checkpoint_every=ck)
+        if ck:
+            m0, m1 = mass(u0, L, L), mass(out.detach(), L, L)
+            assert abs(m1 / m0 - 1.0) < 1e-12
+        loss_of(out).backward()
+        grads.append(u.grad.clone())
+    assert torch.allclose(grads[0], grads[1], rtol=0, atol=1e-12 * float(grads[1].abs().max()))
+    # central difference along one direction (fewer steps keep it quick)
+    gen = torch.Generator(device="cpu").manual_seed(9)
+    d = torch.complex(torch.randn(n, n, generator=gen, dtype=torch.float64),
+                      torch.randn(n, n, generator=gen, dtype=torch.float64)).cuda()
+    k = 10
+    u = u0.clone().requires_grad_(True)
+    loss_of(evolve(u, k, ds, solver, tau, 1.0, 1.0, checkpoint_every=4)).backward()
+    an = float((u.grad.real * d.real + u.grad.imag * d.imag).sum())
+    h = 1e-6
+    with torch.no_grad():
+        fp = float(loss_of(evolve(u0 + h * d, k, ds, solver, tau, 1.0, 1.0)))
+        fm = float(loss_of(evolve(u0 - h * d, k, ds, solver, tau, 1.0, 1.0)))
+    fd = (fp - fm) / (2 * h)
+    assert abs(fd - an) <= 1e-6 * abs(an)
+    solver.close()
+    ds.close()
+
+
+def test_ds_loop_complex64_gradient_vs_complex128():
+    """complex64 (mixed plans) gradient agrees with the complex128 one."""
+    from paper_1409_2014_gb300.ds import evolve
+
+    n, L, tau, steps = 256, 16.0, 1e-3, 20
+    grads = {}
+    for prec in ("fp64", "mixed"):
+        solver, ds = _plans(n, L, prec, P=6.0, n_r=32, n_theta=64, sigma=1.0)
+        u0 = torch.from_numpy(synth.wavefunction_sum(n, n, L, L, seed=3, count=8)).to(CDT[prec]).cuda()
+        w = torch.from_numpy(synth.normal_field(n, n, seed=4)).cuda()
+        u = u0.clone().requires_grad_(True)
+        out = evolve(u, steps, ds, solver, tau, 1.0, 1.0, checkpoint_every=5)
+        (w * (out.real.double() ** 2 + out.imag.double() ** 2)).sum().backward()
+        grads[prec] = u.grad.to(torch.complex128).cpu().numpy()
+        solver.close()
+        ds.close()
+    ref = grads["fp64"]
+    assert np.abs(grads["mixed"] - ref).max() <= 1e-4 * np.abs(ref).max()
