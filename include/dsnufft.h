@@ -235,6 +235,44 @@ dsnu_status dsnu_ds_nonlinear_vjp_finish(dsnu_ds_plan plan, const void* u_dev, c
 
 dsnu_status dsnu_ds_plan_destroy(dsnu_ds_plan plan);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many densities, possibly on different grids, per launch sequence.
+ * Members that share a plan are solved together (each kernel runs once for the
+ * group, its CTAs iterating over members and work items); distinct plans run
+ * on forked streams.  Results are bitwise identical to one dsnu_solve per
+ * member.
+ * ------------------------------------------------------------------------- */
+typedef struct dsnu_batch_s* dsnu_batch;
+
+/* count members; plans[i] is member i's plan (plans may repeat).  The batch
+ * keeps the plan handles: they must outlive it.  Creates one stream and one
+ * event per distinct plan and a small device table per plan.
+ * Errors: DSNU_EINVAL, DSNU_ECUDA. */
+dsnu_status dsnu_batch_create(int32_t count, const dsnu_plan* plans, dsnu_batch* out);
+
+/* Device scratch for all members (sum of the members' workspaces, 256-byte
+ * aligned each). */
+size_t dsnu_batch_workspace_bytes(dsnu_batch b);
+
+/* Bind the members' device buffers: rho_dev[i] (FP64 [ny_i][nx_i], read) and
+ * phi_dev[i] (written), and the caller-owned batch workspace (>=
+ * dsnu_batch_workspace_bytes, 256-byte aligned).  Uploads the member tables
+ * on `stream` and synchronises it; drops a previously captured graph.
+ * Errors: DSNU_EINVAL, DSNU_ECUDA. */
+dsnu_status dsnu_batch_bind(dsnu_batch b, const double* const* rho_dev, double* const* phi_dev,
+                            void* workspace_dev, size_t bytes, void* stream);
+
+/* Capture the batch's launch sequence (all groups, forked streams joined back
+ * to `stream`) into a CUDA graph, instantiated once; dsnu_batch_solve then
+ * replays it.  `stream` must not be capturing already. */
+dsnu_status dsnu_batch_capture_graph(dsnu_batch b, void* stream);
+
+/* Solve every member: graph replay when captured, else the launches.  Only
+ * launches (no allocation, no synchronisation). */
+dsnu_status dsnu_batch_solve(dsnu_batch b, void* stream);
+
+dsnu_status dsnu_batch_destroy(dsnu_batch b);
+
 /* Plan introspection for tests and benchmarks (host values, no device work). */
 typedef struct {
   int32_t n_nodes;       /* n_r * n_theta */

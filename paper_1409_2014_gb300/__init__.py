@@ -137,3 +137,56 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many densities per launch sequence (members may use different plans).
+
+    ``Batch(plans, rhos, phis)`` binds device tensors; ``solve()`` runs every
+    member; ``capture_graph()`` records the launch sequence as a CUDA graph
+    that ``solve()`` then replays."""
+
+    def __init__(self, plans, rhos, phis):
+        import torch
+
+        if not (len(plans) == len(rhos) == len(phis)) or not plans:
+            raise ValueError("plans, rhos and phis must have the same, non-zero length")
+        for p, r, f in zip(plans, rhos, phis):
+            p._check_input(r)
+            p._check_input(f)
+        self.plans, self.rhos, self.phis = list(plans), list(rhos), list(phis)
+        self.device = plans[0].device
+        self._h = _abi.dsnu_batch_create([p.handle for p in plans])
+        nbytes = _abi.dsnu_batch_workspace_bytes(self._h)
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        _abi.dsnu_batch_bind(self._h, [r.data_ptr() for r in rhos], [f.data_ptr() for f in phis],
+                             self.workspace.data_ptr(), self.workspace.numel(),
+                             torch.cuda.current_stream(self.device).cuda_stream)
+
+    def capture_graph(self):
+        import torch
+
+        s = torch.cuda.Stream(self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        _abi.dsnu_batch_capture_graph(self._h, s.cuda_stream)
+        torch.cuda.current_stream(self.device).wait_stream(s)
+
+    def solve(self):
+        import torch
+
+        _abi.dsnu_batch_solve(self._h, torch.cuda.current_stream(self.device).cuda_stream)
+        return self.phis
+
+    def close(self):
+        if getattr(self, "_h", None):
+            import torch
+
+            torch.cuda.synchronize(self.device)
+            _abi.dsnu_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

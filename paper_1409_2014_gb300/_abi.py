@@ -27,6 +27,8 @@ EXPORTED = [
     "dsnu_stage_count", "dsnu_stage_name", "dsnu_solve_noalloc", "dsnu_noalloc_scratch_bytes",
     "dsnu_ds_plan_create", "dsnu_ds_set_linear_step", "dsnu_ds_linear", "dsnu_ds_abs2",
     "dsnu_ds_nonlinear", "dsnu_ds_nonlinear_vjp", "dsnu_ds_nonlinear_vjp_finish", "dsnu_ds_plan_destroy",
+    "dsnu_batch_create", "dsnu_batch_workspace_bytes", "dsnu_batch_bind", "dsnu_batch_capture_graph",
+    "dsnu_batch_solve", "dsnu_batch_destroy",
 ]
 
 
@@ -122,6 +124,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("dsnu_ds_plan_create", "dsnu_ds_set_linear_step", "dsnu_ds_linear", "dsnu_ds_abs2",
                  "dsnu_ds_nonlinear", "dsnu_ds_nonlinear_vjp", "dsnu_ds_nonlinear_vjp_finish",
                  "dsnu_ds_plan_destroy"):
+        getattr(lib, name).restype = st
+    lib.dsnu_batch_create.argtypes = [ctypes.c_int32, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    lib.dsnu_batch_workspace_bytes.argtypes = [vp]
+    lib.dsnu_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.dsnu_batch_bind.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, ctypes.c_size_t, vp]
+    lib.dsnu_batch_capture_graph.argtypes = [vp, vp]
+    lib.dsnu_batch_solve.argtypes = [vp, vp]
+    lib.dsnu_batch_destroy.argtypes = [vp]
+    for name in ("dsnu_batch_create", "dsnu_batch_bind", "dsnu_batch_capture_graph", "dsnu_batch_solve",
+                 "dsnu_batch_destroy"):
         getattr(lib, name).restype = st
     _LIB = lib
     return lib
@@ -264,3 +276,32 @@ def dsnu_ds_nonlinear_vjp_finish(plan, u, s, ats, tau, beta, grad, stream=0) -> 
 
 def dsnu_ds_plan_destroy(plan: int) -> None:
     _check(load().dsnu_ds_plan_destroy(_vp(plan)), "dsnu_ds_plan_destroy")
+
+
+def dsnu_batch_create(plans) -> int:
+    arr = (ctypes.c_void_p * len(plans))(*plans)
+    out = ctypes.c_void_p()
+    _check(load().dsnu_batch_create(len(plans), arr, ctypes.byref(out)), "dsnu_batch_create")
+    return out.value
+
+
+def dsnu_batch_workspace_bytes(batch: int) -> int:
+    return int(load().dsnu_batch_workspace_bytes(_vp(batch)))
+
+
+def dsnu_batch_bind(batch: int, rho_ptrs, phi_ptrs, ws: int, nbytes: int, stream: int = 0) -> None:
+    r = (ctypes.c_void_p * len(rho_ptrs))(*rho_ptrs)
+    p = (ctypes.c_void_p * len(phi_ptrs))(*phi_ptrs)
+    _check(load().dsnu_batch_bind(_vp(batch), r, p, _vp(ws), nbytes, _vp(stream)), "dsnu_batch_bind")
+
+
+def dsnu_batch_capture_graph(batch: int, stream: int = 0) -> None:
+    _check(load().dsnu_batch_capture_graph(_vp(batch), _vp(stream)), "dsnu_batch_capture_graph")
+
+
+def dsnu_batch_solve(batch: int, stream: int = 0) -> None:
+    _check(load().dsnu_batch_solve(_vp(batch), _vp(stream)), "dsnu_batch_solve")
+
+
+def dsnu_batch_destroy(batch: int) -> None:
+    _check(load().dsnu_batch_destroy(_vp(batch)), "dsnu_batch_destroy")

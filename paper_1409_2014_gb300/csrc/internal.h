@@ -39,6 +39,21 @@ struct PlanTables {
 
 
 
+// One density of a (possibly batched) launch: input, output and the base of
+// its workspace (laid out by WsLayout).
+struct Member {
+  const double* rho;
+  double* phi;
+  char* ws;
+};
+
+// The members of a launch: `one` when count == 1, else a device array.
+struct Members {
+  const Member* dev;
+  Member one;
+  int count;
+};
+
 // Workspace layout (offsets in bytes from the workspace base).
 struct WsLayout {
   size_t off_A, off_B, off_Bband, off_Sband, off_c, off_partial, total;
@@ -50,7 +65,7 @@ struct PlanGeom {
   int log2lo_x, log2lo_y;  // two-level e^{-2 pi i n/M} tables
   int n_gy;                // entries of the short partition table
   double dky2;             // dk_y^2
-  int grid_rowf, grid_col, grid_bandf, grid_bandi, grid_rowi;  // persistent grid sizes
+  int cap_rowf, cap_col, cap_bandf, cap_bandi, cap_rowi;  // resident CTAs (SMs x occupancy)
   int w, Q, n_nodes, n_tiles, tiles_x, tiles_y, max_tile_nodes, n_items;
   int precision, sharp;
   double beta, sigma, cut_radius;
@@ -62,12 +77,21 @@ constexpr int kProfEvents = kStages + 1;  // events per profiled solve (see run_
 
 // Launchers (one translation unit per precision).  `ev`, when not NULL,
 // holds kProfEvents events recorded around the kernels.
-dsnu_status run_pipeline_f32(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
-                             const double* rho, double* phi, cudaStream_t st, int cj,
-                             cudaEvent_t* ev);
-dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
-                             const double* rho, double* phi, cudaStream_t st, int cj,
-                             cudaEvent_t* ev);
+dsnu_status run_pipeline_f32(const PlanGeom& g, const PlanTables& t, const WsLayout& L,
+                             const Members& mem, cudaStream_t st, int cj, cudaEvent_t* ev);
+dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L,
+                             const Members& mem, cudaStream_t st, int cj, cudaEvent_t* ev);
+
+// A single density as a one-member launch.
+inline Members single_member(const double* rho, double* phi, void* ws) {
+  Members m;
+  m.dev = nullptr;
+  m.one.rho = rho;
+  m.one.phi = phi;
+  m.one.ws = static_cast<char*>(ws);
+  m.count = 1;
+  return m;
+}
 // Set the kernels' shared-memory limits and compute persistent grid sizes.
 cudaError_t prepare_kernels_f32(PlanGeom& g);
 cudaError_t prepare_kernels_f64(PlanGeom& g);

@@ -37,6 +37,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "internal.h"
 
 // Occupancy targets (minimum resident CTAs per SM) and the FP32 forward-row
 // tile height; overridable at compile time for tuning sweeps.
@@ -106,6 +107,16 @@ __device__ __forceinline__ R mult_high(const MultTabs<R>& mt, R wx2, R gx, int q
   return -fdiv(wx2, s) * part;
 }
 
+// Workspace offsets (bytes) of one member's buffers, and member access.
+struct WsOff {
+  size_t A, B, Bband, Sband, c, partial;
+};
+__device__ __forceinline__ Member member_at(const Members& m, int i) { return m.count == 1 ? m.one : m.dev[i]; }
+template <typename T>
+__device__ __forceinline__ T* ws_ptr(const Member& mb, size_t off) {
+  return reinterpret_cast<T*>(mb.ws + off);
+}
+
 // Row tiling of the intermediate spectra (see the file comment).
 template <typename R>
 struct Tile {
@@ -163,8 +174,7 @@ struct Geo {
 // ---------------------------------------------------------------------------
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_RF, min_blocks<R>(DSNU_ROW_MINB))
-k_row_fwd(const double* __restrict__ rho, cpx<R>* __restrict__ A, int ldqA,
-          cpx<R>* __restrict__ B, int ldqB, int Q, int ny, AxisTabs<R> ax,
+k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
           const R* __restrict__ decon_y, int cj) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, RB = GG::RB_F, T = GG::T_RF, RS = GG::RS;
@@ -178,7 +188,12 @@ k_row_fwd(const double* __restrict__ rho, cpx<R>* __restrict__ A, int ldqA,
   const R isg = cj ? R(-1) : R(1);
   const int items = (ny + RB - 1) / RB;
 #pragma unroll 1
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+    const int mi = it / items, item = it - mi * items;
+    const Member mb = member_at(mem, mi);
+    const double* __restrict__ rho = mb.rho;
+    cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(mb, off.A);
+    cpx<R>* __restrict__ B = ws_ptr<cpx<R>>(mb, off.B);
     const int row0 = item * RB;
 #pragma unroll 1
     for (int par = 0; par < 2; ++par) {
@@ -237,7 +252,7 @@ k_row_fwd(const double* __restrict__ rho, cpx<R>* __restrict__ A, int ldqA,
 // is safe.
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
-k_col_main(cpx<R>* __restrict__ A, int ldqA, int ncols, AxisTabs<R> ay, MultTabs<R> mt, int cj) {
+k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs<R> mt, int cj) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, CC = GG::CC, FB = GG::FB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -251,7 +266,9 @@ k_col_main(cpx<R>* __restrict__ A, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
   cpx<R>* held = sm + CC * FB + cl * N;  // even-chain result, index n
   const int items = (ncols + CC - 1) / CC;
 #pragma unroll 1
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+    const int mi = it / items, item = it - mi * items;
+    cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(member_at(mem, mi), off.A);
     const int col = item * CC + cl;
     const bool valid = col < ncols;
     const R wx2 = valid ? mt.wx2[col] : R(0);
@@ -296,8 +313,7 @@ k_col_main(cpx<R>* __restrict__ A, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
 // ---------------------------------------------------------------------------
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
-k_band_fwd(const cpx<R>* __restrict__ B, int ldqB, int ncols, cpx<R>* __restrict__ Bband, int ldq,
-           int Q, AxisTabs<R> ay, int cj) {
+k_band_fwd(Members mem, WsOff off, int ldqB, int ncols, int ldq, int Q, AxisTabs<R> ay, int cj) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, M = GG::M, G = GG::G, CC = GG::CC, FB = GG::FB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -310,7 +326,11 @@ k_band_fwd(const cpx<R>* __restrict__ B, int ldqB, int ncols, cpx<R>* __restrict
   cpx<R>* buf = sm + cl * FB;
   const int items = (ncols + CC - 1) / CC;
 #pragma unroll 1
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+    const int mi = it / items, item = it - mi * items;
+    const Member mb = member_at(mem, mi);
+    const cpx<R>* __restrict__ B = ws_ptr<cpx<R>>(mb, off.B);
+    cpx<R>* __restrict__ Bband = ws_ptr<cpx<R>>(mb, off.Bband);
     const int col = item * CC + cl;
     const bool valid = col < ncols;
 #pragma unroll 1
@@ -344,9 +364,11 @@ k_band_fwd(const cpx<R>* __restrict__ B, int ldqB, int ncols, cpx<R>* __restrict
 // Type-2 interpolation: one warp per polar node.
 template <typename R>
 __global__ void __launch_bounds__(256)
-k_interp(const cpx<R>* __restrict__ Bband, int ldq, int Q, const int2* __restrict__ q0,
-         const R* __restrict__ wts, const double* __restrict__ D, int n_nodes, int w,
-         cpx<R>* __restrict__ c, int cj) {
+k_interp(Members mem, WsOff off, int ldq, int Q, const int2* __restrict__ q0,
+         const R* __restrict__ wts, const double* __restrict__ D, int n_nodes, int w, int cj) {
+  const Member mb = member_at(mem, blockIdx.y);
+  const cpx<R>* __restrict__ Bband = ws_ptr<cpx<R>>(mb, off.Bband);
+  cpx<R>* __restrict__ c = ws_ptr<cpx<R>>(mb, off.c);
   const int lane = threadIdx.x & 31;
   const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (j >= n_nodes) return;
@@ -396,10 +418,12 @@ constexpr int kSpreadChunk = 128;
 
 template <typename R>
 __global__ void __launch_bounds__(kSpreadThreads)
-k_spread(const cpx<R>* __restrict__ c, const int2* __restrict__ item_range,
+k_spread(Members mem, WsOff off, const int2* __restrict__ item_range,
          const int* __restrict__ ent_node, const int2* __restrict__ ent_q0,
-         const R* __restrict__ ent_w, const int* __restrict__ item_tile, int w, int tiles_x, int Q,
-         cpx<R>* __restrict__ partial) {
+         const R* __restrict__ ent_w, const int* __restrict__ item_tile, int w, int tiles_x, int Q) {
+  const Member mb = member_at(mem, blockIdx.y);
+  const cpx<R>* __restrict__ c = ws_ptr<cpx<R>>(mb, off.c);
+  cpx<R>* __restrict__ partial = ws_ptr<cpx<R>>(mb, off.partial);
   __shared__ int2 s_q0[kSpreadChunk];
   __shared__ cpx<R> s_c[kSpreadChunk];
   __shared__ R s_w[kSpreadChunk * 32];
@@ -447,8 +471,11 @@ k_spread(const cpx<R>* __restrict__ c, const int2* __restrict__ item_range,
 
 template <typename R>
 __global__ void __launch_bounds__(kTile * kTile)
-k_spread_reduce(const cpx<R>* __restrict__ partial, const int* __restrict__ tile_items, int tiles_x,
-                int n_tiles, int Q, cpx<R>* __restrict__ Sband, int ldq, int cj) {
+k_spread_reduce(Members mem, WsOff off, const int* __restrict__ tile_items, int tiles_x,
+                int n_tiles, int Q, int ldq, int cj) {
+  const Member mb = member_at(mem, blockIdx.y);
+  const cpx<R>* __restrict__ partial = ws_ptr<cpx<R>>(mb, off.partial);
+  cpx<R>* __restrict__ Sband = ws_ptr<cpx<R>>(mb, off.Sband);
   const int tile = blockIdx.x;
   if (tile >= n_tiles) return;
   const int cell = threadIdx.x;
@@ -470,8 +497,7 @@ k_spread_reduce(const cpx<R>* __restrict__ partial, const int* __restrict__ tile
 // ---------------------------------------------------------------------------
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
-k_band_inv(const cpx<R>* __restrict__ Sband, int ldq, int Q, int ncols, cpx<R>* __restrict__ St,
-           int ldqB, AxisTabs<R> ay, int cj) {
+k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs<R> ay, int cj) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, M = GG::M, G = GG::G, CC = GG::CC, FB = GG::FB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -484,7 +510,11 @@ k_band_inv(const cpx<R>* __restrict__ Sband, int ldq, int Q, int ncols, cpx<R>* 
   cpx<R>* held = sm + CC * FB + cl * N;
   const int items = (ncols + CC - 1) / CC;
 #pragma unroll 1
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+    const int mi = it / items, item = it - mi * items;
+    const Member mb = member_at(mem, mi);
+    const cpx<R>* __restrict__ Sband = ws_ptr<cpx<R>>(mb, off.Sband);
+    cpx<R>* __restrict__ St = ws_ptr<cpx<R>>(mb, off.B);
     const int col = item * CC + cl;
     const bool valid = col < ncols;
 #pragma unroll 1
@@ -520,9 +550,8 @@ k_band_inv(const cpx<R>* __restrict__ Sband, int ldq, int Q, int ncols, cpx<R>* 
 // with W(q) = Y(q) + i S(q) for q <= N and W(M - q) = conj Y(q) + i conj S(q).
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(Geo<R, LOG2N>::T_RI > 512 ? 1 : DSNU_ROW_MINB))
-k_row_inv(const cpx<R>* __restrict__ A, int ldqA, const cpx<R>* __restrict__ St, int ldqB, int Q,
-          double* __restrict__ phi, int ny, AxisTabs<R> ax, const R* __restrict__ decon_y, R scale,
-          int cj) {
+k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
+          const R* __restrict__ decon_y, R scale, int cj) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, RB = GG::RB_I, T = GG::T_RI, RS = GG::RS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -535,7 +564,12 @@ k_row_inv(const cpx<R>* __restrict__ A, int ldqA, const cpx<R>* __restrict__ St,
   cpx<R>* buf = sm + rr * RS;
   const int items = (ny + RB - 1) / RB;
 #pragma unroll 1
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+    const int mi = it / items, item = it - mi * items;
+    const Member mb = member_at(mem, mi);
+    const cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(mb, off.A);
+    const cpx<R>* __restrict__ St = ws_ptr<cpx<R>>(mb, off.B);
+    double* __restrict__ phi = mb.phi;
     const int row0 = item * RB;
     const int row = row0 + rr;
     const bool valid = row < ny;

@@ -94,10 +94,10 @@ dsnu_status dsnu_solve_noalloc(dsnu_plan plan, const double* rho, double* phi, v
   // solve, so nothing in the scratch needs clearing between calls.
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (plan->geom.precision == DSNU_MIXED)
-    return dsnu::run_pipeline_f32(plan->geom, plan->tab, plan->ws_layout, scratch, rho, phi, st, 0,
-                                  nullptr);
-  return dsnu::run_pipeline_f64(plan->geom, plan->tab, plan->ws_layout, scratch, rho, phi, st, 0,
-                                nullptr);
+    return dsnu::run_pipeline_f32(plan->geom, plan->tab, plan->ws_layout,
+                                  dsnu::single_member(rho, phi, scratch), st, 0, nullptr);
+  return dsnu::run_pipeline_f64(plan->geom, plan->tab, plan->ws_layout, dsnu::single_member(rho, phi, scratch),
+                                st, 0, nullptr);
 }
 
 }  // extern "C"

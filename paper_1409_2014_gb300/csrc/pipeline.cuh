@@ -17,17 +17,22 @@ namespace dsnu {
   case 11: CALL(11); break;   \
   case 12: CALL(12); break;
 
+// Number of CTAs of `kernel` that can be resident at once (SMs x occupancy).
 template <typename K>
-static cudaError_t persistent_grid(K kernel, int threads, size_t smem, int items, int* grid) {
+static cudaError_t resident_ctas(K kernel, int threads, size_t smem, int* cap) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int cap = sms * per_sm;
-  *grid = items < cap ? (items > 0 ? items : 1) : cap;
+  *cap = sms * per_sm;
   return cudaSuccess;
+}
+
+// Persistent grid: one CTA per work item up to the resident capacity.
+static inline int persistent_grid(long items, int cap) {
+  return items < cap ? (items > 0 ? int(items) : 1) : cap;
 }
 
 template <typename R, int L2>
@@ -38,10 +43,8 @@ cudaError_t prepare_rows(PlanGeom& g) {
                                 int(GG::smem_row_fwd)))) return e;
   if ((e = cudaFuncSetAttribute(k_row_inv<R, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(GG::smem_row_inv)))) return e;
-  if ((e = persistent_grid(k_row_fwd<R, L2>, GG::T_RF, GG::smem_row_fwd,
-                           (g.ny + GG::RB_F - 1) / GG::RB_F, &g.grid_rowf))) return e;
-  return persistent_grid(k_row_inv<R, L2>, GG::T_RI, GG::smem_row_inv, (g.ny + GG::RB_I - 1) / GG::RB_I,
-                         &g.grid_rowi);
+  if ((e = resident_ctas(k_row_fwd<R, L2>, GG::T_RF, GG::smem_row_fwd, &g.cap_rowf))) return e;
+  return resident_ctas(k_row_inv<R, L2>, GG::T_RI, GG::smem_row_inv, &g.cap_rowi);
 }
 
 template <typename R, int L2>
@@ -52,12 +55,9 @@ cudaError_t prepare_cols(PlanGeom& g) {
   if ((e = cudaFuncSetAttribute(k_col_main<R, L2>, A, int(GG::smem_col)))) return e;
   if ((e = cudaFuncSetAttribute(k_band_fwd<R, L2>, A, int(GG::smem_band_fwd)))) return e;
   if ((e = cudaFuncSetAttribute(k_band_inv<R, L2>, A, int(GG::smem_col)))) return e;
-  if ((e = persistent_grid(k_col_main<R, L2>, GG::T_C, GG::smem_col, (g.nx + 1 + GG::CC - 1) / GG::CC,
-                           &g.grid_col))) return e;
-  if ((e = persistent_grid(k_band_fwd<R, L2>, GG::T_C, GG::smem_band_fwd, (g.Q + 1 + GG::CC - 1) / GG::CC,
-                           &g.grid_bandf))) return e;
-  return persistent_grid(k_band_inv<R, L2>, GG::T_C, GG::smem_col, (g.Q + 1 + GG::CC - 1) / GG::CC,
-                         &g.grid_bandi);
+  if ((e = resident_ctas(k_col_main<R, L2>, GG::T_C, GG::smem_col, &g.cap_col))) return e;
+  if ((e = resident_ctas(k_band_fwd<R, L2>, GG::T_C, GG::smem_band_fwd, &g.cap_bandf))) return e;
+  return resident_ctas(k_band_inv<R, L2>, GG::T_C, GG::smem_col, &g.cap_bandi);
 }
 
 template <typename R>
@@ -84,14 +84,9 @@ cudaError_t prepare_kernels(PlanGeom& g) {
 // (profiling) kProfEvents events are recorded before the first kernel and
 // after each kernel, in launch order.
 template <typename R>
-dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
-                         const double* rho, double* phi, cudaStream_t st, int cj, cudaEvent_t* ev) {
-  char* base = static_cast<char*>(ws);
-  cpx<R>* A = reinterpret_cast<cpx<R>*>(base + L.off_A);
-  cpx<R>* B = reinterpret_cast<cpx<R>*>(base + L.off_B);
-  cpx<R>* Bband = reinterpret_cast<cpx<R>*>(base + L.off_Bband);
-  cpx<R>* Sband = reinterpret_cast<cpx<R>*>(base + L.off_Sband);
-  cpx<R>* cn = reinterpret_cast<cpx<R>*>(base + L.off_c);
+dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout& L, const Members& mem,
+                         cudaStream_t st, int cj, cudaEvent_t* ev) {
+  const WsOff off{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial};
   const AxisTabs<R> ax{static_cast<const cpx<R>*>(t.stw_x), static_cast<const cpx<R>*>(t.twm_lo_x),
                        static_cast<const cpx<R>*>(t.twm_hi_x), g.log2lo_x, static_cast<const R*>(t.decon_x)};
   const AxisTabs<R> ay{static_cast<const cpx<R>*>(t.stw_y), static_cast<const cpx<R>*>(t.twm_lo_y),
@@ -103,23 +98,32 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
   const R* dcy = static_cast<const R*>(t.decon_y);
   const R* wts = static_cast<const R*>(t.node_w);
   const int ldqA = L.ldqA, ldqB = L.ldqB;
+  const long nm = mem.count;
 
 #define DSNU_ROWF(L2)                                                                               \
-  k_row_fwd<R, L2><<<g.grid_rowf, Geo<R, L2>::T_RF,                                               \
-                     Geo<R, L2>::smem_row_fwd, st>>>(rho, A, ldqA, B, ldqB, g.Q, g.ny, ax, dcy, cj)
-#define DSNU_COLM(L2)                                                                                 \
-  k_col_main<R, L2><<<g.grid_col, Geo<R, L2>::T_C,                                                 \
-                      Geo<R, L2>::smem_col, st>>>(A, ldqA, g.nx + 1, ay, mt, cj)
-#define DSNU_BANDF(L2)                                                                                \
-  k_band_fwd<R, L2><<<g.grid_bandf, Geo<R, L2>::T_C,                                               \
-                      Geo<R, L2>::smem_band_fwd, st>>>(B, ldqB, g.Q + 1, Bband, L.ldq, g.Q, ay, cj)
-#define DSNU_BANDI(L2)                                                                                \
-  k_band_inv<R, L2><<<g.grid_bandi, Geo<R, L2>::T_C,                                               \
-                      Geo<R, L2>::smem_col, st>>>(Sband, L.ldq, g.Q, g.Q + 1, B, ldqB, ay, cj)
-#define DSNU_ROWI(L2)                                                                                 \
-  k_row_inv<R, L2><<<g.grid_rowi, Geo<R, L2>::T_RI,                                                \
-                     Geo<R, L2>::smem_row_inv, st>>>(A, ldqA, B, ldqB, g.Q, phi, g.ny, ax, dcy,     \
-                                                     R(g.scale), cj)
+  k_row_fwd<R, L2><<<persistent_grid(nm * ((g.ny + Geo<R, L2>::RB_F - 1) / Geo<R, L2>::RB_F),       \
+                                     g.cap_rowf),                                                    \
+                     Geo<R, L2>::T_RF, Geo<R, L2>::smem_row_fwd, st>>>(mem, off, ldqA, ldqB, g.Q,    \
+                                                                       g.ny, ax, dcy, cj)
+#define DSNU_COLM(L2)                                                                               \
+  k_col_main<R, L2><<<persistent_grid(nm * ((g.nx + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC),      \
+                                      g.cap_col),                                                    \
+                      Geo<R, L2>::T_C, Geo<R, L2>::smem_col, st>>>(mem, off, ldqA, g.nx + 1, ay, mt, cj)
+#define DSNU_BANDF(L2)                                                                              \
+  k_band_fwd<R, L2><<<persistent_grid(nm * ((g.Q + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC),       \
+                                      g.cap_bandf),                                                  \
+                      Geo<R, L2>::T_C, Geo<R, L2>::smem_band_fwd, st>>>(mem, off, ldqB, g.Q + 1, L.ldq, \
+                                                                         g.Q, ay, cj)
+#define DSNU_BANDI(L2)                                                                              \
+  k_band_inv<R, L2><<<persistent_grid(nm * ((g.Q + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC),       \
+                                      g.cap_bandi),                                                  \
+                      Geo<R, L2>::T_C, Geo<R, L2>::smem_col, st>>>(mem, off, L.ldq, g.Q, g.Q + 1, ldqB, \
+                                                                    ay, cj)
+#define DSNU_ROWI(L2)                                                                               \
+  k_row_inv<R, L2><<<persistent_grid(nm * ((g.ny + Geo<R, L2>::RB_I - 1) / Geo<R, L2>::RB_I),       \
+                                     g.cap_rowi),                                                    \
+                     Geo<R, L2>::T_RI, Geo<R, L2>::smem_row_inv, st>>>(mem, off, ldqA, ldqB, g.Q,    \
+                                                                       g.ny, ax, dcy, R(g.scale), cj)
 #define DSNU_MARK(I) \
   if (ev) cudaEventRecord(ev[I], st)
   DSNU_MARK(0);
@@ -133,17 +137,16 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
     default: return DSNU_EUNSUPPORTED;
   }
   DSNU_MARK(2);
-  k_interp<R><<<(g.n_nodes + 7) / 8, 256, 0, st>>>(Bband, L.ldq, g.Q, t.node_q0, wts, t.node_D,
-                                                   g.n_nodes, g.w, cn, cj);
+  k_interp<R><<<dim3((g.n_nodes + 7) / 8, mem.count), 256, 0, st>>>(mem, off, L.ldq, g.Q, t.node_q0, wts,
+                                                                     t.node_D, g.n_nodes, g.w, cj);
   DSNU_MARK(3);
-  cpx<R>* partial = reinterpret_cast<cpx<R>*>(base + L.off_partial);
   if (g.n_items > 0)
-    k_spread<R><<<g.n_items, kSpreadThreads, 0, st>>>(cn, t.item_range, t.ent_node, t.ent_q0,
-                                                      static_cast<const R*>(t.ent_w), t.item_tile, g.w,
-                                                      g.tiles_x, g.Q, partial);
+    k_spread<R><<<dim3(g.n_items, mem.count), kSpreadThreads, 0, st>>>(
+        mem, off, t.item_range, t.ent_node, t.ent_q0, static_cast<const R*>(t.ent_w), t.item_tile, g.w,
+        g.tiles_x, g.Q);
   DSNU_MARK(4);
-  k_spread_reduce<R><<<g.n_tiles, kTile * kTile, 0, st>>>(partial, t.tile_items, g.tiles_x, g.n_tiles,
-                                                         g.Q, Sband, L.ldq, cj);
+  k_spread_reduce<R><<<dim3(g.n_tiles, mem.count), kTile * kTile, 0, st>>>(mem, off, t.tile_items, g.tiles_x,
+                                                                            g.n_tiles, g.Q, L.ldq, cj);
   DSNU_MARK(5);
   switch (g.log2ny) {
     DSNU_LOG2_CASES(DSNU_BANDI)

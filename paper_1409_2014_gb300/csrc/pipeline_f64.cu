@@ -2,10 +2,9 @@
 #include "pipeline.cuh"
 
 namespace dsnu {
-dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws,
-                             const double* rho, double* phi, cudaStream_t st, int cj,
-                             cudaEvent_t* ev) {
-  return run_pipeline<double>(g, t, L, ws, rho, phi, st, cj, ev);
+dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L,
+                             const Members& mem, cudaStream_t st, int cj, cudaEvent_t* ev) {
+  return run_pipeline<double>(g, t, L, mem, st, cj, ev);
 }
 cudaError_t prepare_kernels_f64(PlanGeom& g) { return prepare_kernels<double>(g); }
 }  // namespace dsnu

@@ -481,8 +481,10 @@ static dsnu_status run(dsnu_plan plan, const double* in, double* out, void* stre
   if (plan->prof_events && plan->prof_used < plan->prof_max)
     ev = plan->prof_events + size_t(plan->prof_used++) * kProfEvents;
   if (plan->geom.precision == DSNU_MIXED)
-    return run_pipeline_f32(plan->geom, plan->tab, plan->ws_layout, plan->ws, in, out, st, cj, ev);
-  return run_pipeline_f64(plan->geom, plan->tab, plan->ws_layout, plan->ws, in, out, st, cj, ev);
+    return run_pipeline_f32(plan->geom, plan->tab, plan->ws_layout, single_member(in, out, plan->ws), st,
+                            cj, ev);
+  return run_pipeline_f64(plan->geom, plan->tab, plan->ws_layout, single_member(in, out, plan->ws), st, cj,
+                          ev);
 }
 
 static void free_profile(dsnu_plan plan) {
