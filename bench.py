@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle run (no accuracy / cpu_baseline keys)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-member batch measurement")
     ap.add_argument("--only-timed", action="store_true",
                     help="run only warmup + the timed mixed region (for profiler launch lists)")
     return ap.parse_args()
@@ -250,6 +251,59 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_bench(dev, max_over_ranks, barrier, reps=5):
+    """64 seeded densities (4-16 Gaussians) with grids drawn from {256, 512,
+    1024, 2048}^2 on [-32,32)^2, P = 8, 64 x 256 nodes: mixed plans in one
+    batch replayed as a CUDA graph, versus 64 separate FP64 solves."""
+    import torch
+
+    import synth
+    from paper_1409_2014_gb300 import Batch, Plan
+
+    members = synth.batch_members(seed=5, count=64)
+    sizes = sorted({m[0] for m in members})
+    rhos = [torch.from_numpy(synth.density_sum(n, n, 32.0, 32.0, seed=s, count=k)).to(dev)
+            for n, k, s in members]
+    phis = [torch.empty_like(r) for r in rhos]
+    out = {"members": len(members), "sizes": {str(n): sum(1 for m in members if m[0] == n) for n in sizes},
+           "domain": "[-32,32)^2, P=8, 64x256 nodes"}
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for prec in ("mixed", "fp64"):
+        plans = {n: Plan(n, lx=32.0, cut_radius=8.0, n_r=64, n_theta=256, precision=prec, device=dev)
+                 for n in sizes}
+        if prec == "mixed":
+            b = Batch([plans[m[0]] for m in members], rhos, phis)
+            b.capture_graph()
+            b.solve()
+            barrier()
+            e0.record(stream)
+            for _ in range(reps):
+                b.solve()
+            e1.record(stream)
+            barrier()
+            t = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
+            out["mixed_graph_batch"] = {"solves_per_s": reps * len(members) / t, "ms_per_batch": 1e3 * t / reps}
+            b.close()
+        else:
+            for (n, _, _), r, f in zip(members, rhos, phis):
+                plans[n].solve(r, f)
+            barrier()
+            e0.record(stream)
+            for _ in range(reps):
+                for (n, _, _), r, f in zip(members, rhos, phis):
+                    plans[n].solve(r, f)
+            e1.record(stream)
+            barrier()
+            t = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
+            out["fp64_separate"] = {"solves_per_s": reps * len(members) / t, "ms_per_batch": 1e3 * t / reps}
+        for p in plans.values():
+            p.close()
+    out["speedup"] = out["mixed_graph_batch"]["solves_per_s"] / out["fp64_separate"]["solves_per_s"]
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -388,6 +442,9 @@ def run_ours(args):
         "gpu_launches": args.steps * n_stages,
         "clocks": clk,
     }
+
+    if not args.no_batch:
+        line["batch"] = batch_bench(dev, max_over_ranks, barrier)
 
     if rank == 0 and not args.no_cpu_baseline:
         est, phi_ref, desc, _ = oracle_sample(rho_np, 1.0)

@@ -245,6 +245,127 @@ __device__ __forceinline__ void block_fft_regs(cpx<R> (&v)[16], cpx<R>* buf, int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Two independent length-N DFTs (same direction) by the same group of threads:
+// a[m] and b[m] hold x_a[t + G m] and x_b[t + G m]; buffers buf_a and buf_b
+// (fft_buf_elems(N) each).  The stages of both transforms are interleaved, so
+// they share the barriers and every twiddle load, and each thread has two
+// independent butterflies in flight per stage.
+// ---------------------------------------------------------------------------
+template <typename R, int LOG2N, int S>
+__device__ __forceinline__ void fft2_stage_regs(cpx<R> (&a)[16], cpx<R> (&b)[16], cpx<R>* buf_a,
+                                                cpx<R>* buf_b, int t, const cpx<R>* __restrict__ stw) {
+  using SI = StageInfo<LOG2N, S>;
+  constexpr int N = 1 << LOG2N;
+  constexpr int LR = SI::lr;
+  constexpr int RAD = 1 << LR;
+  constexpr int NB = N / RAD;
+  constexpr int G = N / 16;
+  constexpr int PER = 16 / RAD;
+  constexpr int LOG2NS = SI::log2ns;
+  constexpr int NS = 1 << LOG2NS;
+  constexpr bool FIRST = (S == 0);
+  constexpr bool LAST = (S == SI::nstages - 1);
+  if constexpr (!FIRST) {
+    __syncthreads();
+#pragma unroll
+    for (int bb = 0; bb < PER; ++bb) {
+      const int j = t + bb * G;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) {
+        a[bb * RAD + r] = buf_a[pad16(j + r * NB)];
+        b[bb * RAD + r] = buf_b[pad16(j + r * NB)];
+      }
+    }
+  }
+#pragma unroll
+  for (int bb = 0; bb < PER; ++bb) {
+    const int j = t + bb * G;
+    const int k = j & (NS - 1);
+    if constexpr (LOG2NS > 0) {
+      const cpx<R>* tws = stw + SI::tw_off + k;
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        const cpx<R> w = tws[(r - 1) * NS];
+        a[bb * RAD + r] = cmul(a[bb * RAD + r], w);
+        b[bb * RAD + r] = cmul(b[bb * RAD + r], w);
+      }
+    }
+    cpx<R> ua[RAD], ub[RAD];
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) {
+      ua[r] = a[bb * RAD + r];
+      ub[r] = b[bb * RAD + r];
+    }
+    dft_rec<RAD, R>(ua);
+    dft_rec<RAD, R>(ub);
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) {
+      a[bb * RAD + r] = ua[r];
+      b[bb * RAD + r] = ub[r];
+    }
+  }
+  if constexpr (!LAST) {
+    __syncthreads();
+#pragma unroll
+    for (int bb = 0; bb < PER; ++bb) {
+      const int j = t + bb * G;
+      const int k = j & (NS - 1);
+      const int base = (j - k) * RAD + k;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) {
+        buf_a[pad16(base + r * NS)] = a[bb * RAD + r];
+        buf_b[pad16(base + r * NS)] = b[bb * RAD + r];
+      }
+    }
+  } else {
+    cpx<R> oa[16], ob[16];
+#pragma unroll
+    for (int bb = 0; bb < PER; ++bb)
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) {
+        oa[bb + r * PER] = a[bb * RAD + r];
+        ob[bb + r * PER] = b[bb * RAD + r];
+      }
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      a[m] = oa[m];
+      b[m] = ob[m];
+    }
+  }
+}
+
+template <typename R, int LOG2N, int S>
+__device__ __forceinline__ void fft2_stages_regs(cpx<R> (&a)[16], cpx<R> (&b)[16], cpx<R>* buf_a,
+                                                 cpx<R>* buf_b, int t, const cpx<R>* __restrict__ stw) {
+  if constexpr (S < StageInfo<LOG2N, 0>::nstages) {
+    fft2_stage_regs<R, LOG2N, S>(a, b, buf_a, buf_b, t, stw);
+    fft2_stages_regs<R, LOG2N, S + 1>(a, b, buf_a, buf_b, t, stw);
+  }
+}
+
+template <typename R, int LOG2N>
+__device__ __forceinline__ void block_fft2_regs(cpx<R> (&a)[16], cpx<R> (&b)[16], cpx<R>* buf_a,
+                                                cpx<R>* buf_b, int t, const cpx<R>* __restrict__ stw,
+                                                bool inv) {
+  static_assert(LOG2N >= 4 && LOG2N <= 12, "FFT length 16..4096");
+  if (inv) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      a[m].y = -a[m].y;
+      b[m].y = -b[m].y;
+    }
+  }
+  fft2_stages_regs<R, LOG2N, 0>(a, b, buf_a, buf_b, t, stw);
+  if (inv) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      a[m].y = -a[m].y;
+      b[m].y = -b[m].y;
+    }
+  }
+}
+
 // Cooperative copy of `n` table entries from global to shared memory.
 template <typename T>
 __device__ __forceinline__ void copy_to_smem(T* __restrict__ dst, const T* __restrict__ src, int n) {

@@ -39,8 +39,9 @@
 #include "common.cuh"
 #include "internal.h"
 
-// Occupancy targets (minimum resident CTAs per SM) and the FP32 forward-row
-// tile height; overridable at compile time for tuning sweeps.
+// Occupancy targets (minimum resident CTAs per SM), rows per CTA of the FP32
+// row passes and the column-pass variant (both chains paired in registers, or
+// one chain at a time); overridable at compile time for tuning sweeps.
 #ifndef DSNU_ROW_MINB
 #define DSNU_ROW_MINB 2
 #endif
@@ -48,7 +49,16 @@
 #define DSNU_COL_MINB 2
 #endif
 #ifndef DSNU_ROWF_RB32
-#define DSNU_ROWF_RB32 2
+#define DSNU_ROWF_RB32 1
+#endif
+#ifndef DSNU_ROWI_RB32
+#define DSNU_ROWI_RB32 1
+#endif
+#ifndef DSNU_COL_PAIRED
+#define DSNU_COL_PAIRED 1
+#endif
+#ifndef DSNU_COLMAIN_MINB
+#define DSNU_COLMAIN_MINB 1
 #endif
 
 namespace dsnu {
@@ -142,27 +152,23 @@ struct Geo {
   static constexpr int FB = fft_buf_elems(N);        // one FFT buffer
   static constexpr int RS = ((FB + 15) & ~15) + 4;   // row-buffer stride (== 4 mod 16)
   static constexpr int TR = Tile<R>::TR;
-  // forward row pass: RB_F rows per CTA (>= TR), T_RF threads; every group
-  // of G threads transforms RB_F / (T_RF / G) rows one after the other
-  // rows per CTA for small N are capped so that shared memory stays <= ~150 KB
-  static constexpr int RMAX = (sizeof(R) == 4) ? 128 : 64;
-  static constexpr int RB_F0 = (sizeof(R) == 4) ? DSNU_ROWF_RB32 : TR;
+  // row passes: one group of G threads per row, RB_F / RB_I rows per CTA
+  // (more rows for short rows), two transform buffers per row
+  static constexpr int RMAX = (sizeof(R) == 4) ? 64 : 32;
+  static constexpr int RB_F0 = (sizeof(R) == 4) ? DSNU_ROWF_RB32 : 1;
   static constexpr int RB_F = (RB_F0 * G >= 256) ? RB_F0 : ((256 / G < RMAX) ? 256 / G : RMAX);
-  static constexpr int T_RF = (RB_F * G > 512) ? 512 : RB_F * G;
-  static constexpr int RPG_F = RB_F / (T_RF / G);
-  // inverse row pass: RB_I rows per CTA, one group per row
-  static constexpr int RB_I0 = (sizeof(R) == 4) ? ((TR * G >= 256) ? TR : 256 / G)
-                                                : ((G >= 256) ? 1 : 256 / G);
-  static constexpr int RB_I = (RB_I0 < RMAX / 2) ? RB_I0 : RMAX / 2;
+  static constexpr int T_RF = RB_F * G;
+  static constexpr int RB_I0 = (sizeof(R) == 4) ? DSNU_ROWI_RB32 : 1;
+  static constexpr int RB_I = (RB_I0 * G >= 256) ? RB_I0 : ((256 / G < RMAX) ? 256 / G : RMAX);
   static constexpr int T_RI = RB_I * G;
   // column passes: CC columns per CTA
   static constexpr int CC = (G >= 256) ? 1 : 256 / G;
   static constexpr int T_C = CC * G;
   static constexpr int STW = fft_stage_tw_elems(LOG2N) > 0 ? fft_stage_tw_elems(LOG2N) : 1;
   static constexpr int STWP = (STW + 1) & ~1;  // keep the buffers 16-byte aligned
-  static constexpr size_t smem_row_fwd = size_t(STWP + RB_F * RS) * sizeof(cpx<R>);
-  static constexpr size_t smem_row_inv = size_t(STWP + RB_I * RS) * sizeof(cpx<R>);
-  static constexpr size_t smem_col = size_t(STWP + CC * (FB + N)) * sizeof(cpx<R>);  // + held chain
+  static constexpr size_t smem_row_fwd = size_t(STWP + 2 * RB_F * RS) * sizeof(cpx<R>);
+  static constexpr size_t smem_row_inv = size_t(STWP + 2 * RB_I * RS) * sizeof(cpx<R>);
+  static constexpr size_t smem_col = size_t(STWP + 2 * CC * FB) * sizeof(cpx<R>);  // two chains
   static constexpr size_t smem_band_fwd = size_t(STWP + CC * FB) * sizeof(cpx<R>);
   static_assert(LOG2N >= 4 && LOG2N <= 12, "grid size 16..4096");
 };
@@ -172,20 +178,25 @@ struct Geo {
 // stage twiddles in shared memory for the whole launch.
 
 // ---------------------------------------------------------------------------
+// Forward row pass: per row, the even and odd output frequencies of the
+// zero-padded length-M DFT of z = rho + i b are computed together (two
+// interleaved length-N transforms of z and z w_M^n), then the two real-signal
+// spectra are separated at every q in [0, N].
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_RF, min_blocks<R>(DSNU_ROW_MINB))
 k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
           const R* __restrict__ decon_y, int cj) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, RB = GG::RB_F, T = GG::T_RF, RS = GG::RS;
-  constexpr int NG = T / G, RPG = GG::RPG_F;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* sm = stw + GG::STWP;
   copy_to_smem(stw, ax.stw, GG::STW);
   const int tid = threadIdx.x;
-  const int grp = tid / G, t = tid - grp * G;
+  const int rr = tid / G, t = tid - rr * G;
   const R isg = cj ? R(-1) : R(1);
+  cpx<R>* buf_e = sm + (2 * rr) * RS;
+  cpx<R>* buf_o = buf_e + RS;
   const int items = (ny + RB - 1) / RB;
 #pragma unroll 1
   for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
@@ -195,59 +206,118 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(mb, off.A);
     cpx<R>* __restrict__ B = ws_ptr<cpx<R>>(mb, off.B);
     const int row0 = item * RB;
-#pragma unroll 1
-    for (int par = 0; par < 2; ++par) {
-#pragma unroll 1
-      for (int i = 0; i < RPG; ++i) {
-        const int rr = grp + i * NG;  // row within the CTA
-        const int row = row0 + rr;
-        const bool valid = row < ny;
-        const R dy = valid ? decon_y[row] : R(0);
-        cpx<R>* buf = sm + rr * RS;
-        cpx<R> v[16];
+    const int row = row0 + rr;
+    const bool valid = row < ny;
+    const R dy = valid ? decon_y[row] : R(0);
+    cpx<R> e[16], o[16];
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          const int n = t + G * m;
-          const R x = valid ? from_f64<R>(rho[size_t(row) * N + n]) : R(0);
-          cpx<R> z = mk<R>(x, isg * (x * ax.decon[n] * dy));
-          if (par) {
-            cpx<R> w = twm(ax, n);
-            w.y *= isg;
-            z = cmul(z, w);
-          }
-          v[m] = z;
-        }
-        block_fft_regs<R, LOG2N>(v, buf, t, stw, cj != 0);
-        __syncthreads();  // last-stage loads of buf (and the previous unpack) finished
+    for (int m = 0; m < 16; ++m) {
+      const int n = t + G * m;
+      const R x = valid ? from_f64<R>(rho[size_t(row) * N + n]) : R(0);
+      const cpx<R> z = mk<R>(x, isg * (x * ax.decon[n] * dy));
+      cpx<R> w = twm(ax, n);
+      w.y *= isg;
+      e[m] = z;
+      o[m] = cmul(z, w);
+    }
+    block_fft2_regs<R, LOG2N>(e, o, buf_e, buf_o, t, stw, cj != 0);
+    __syncthreads();  // last-stage loads (and the previous unpack) finished
 #pragma unroll
-        for (int m = 0; m < 16; ++m) buf[pad16(t + G * m)] = v[m];
+    for (int m = 0; m < 16; ++m) {
+      buf_e[pad16(t + G * m)] = e[m];
+      buf_o[pad16(t + G * m)] = o[m];
+    }
+    __syncthreads();
+    // separate the spectra at every q in [0, N] (rows fastest):
+    // Z(q) = E[q/2] (q even) or O[(q-1)/2] (q odd); Z(M - q) has the same parity
+    for (int idx = tid; idx < RB * (N + 1); idx += T) {
+      const int r2 = idx & (RB - 1), q = idx / RB, row2 = row0 + r2;
+      if (row2 >= ny) continue;
+      const cpx<R>* be = sm + (2 * r2) * RS;
+      const cpx<R>* bo = be + RS;
+      const int k = q >> 1;
+      cpx<R> zq, zm;
+      if (q & 1) {
+        zq = bo[pad16(k)];
+        zm = bo[pad16(N - 1 - k)];
+      } else {
+        zq = be[pad16(k)];
+        zm = be[pad16(k == 0 ? 0 : N - k)];
       }
-      __syncthreads();
-      // separate the spectra at q = 2k + par, q in [0, N] (rows fastest)
-      const int nk = par ? N / 2 : N / 2 + 1;
-      for (int idx = tid; idx < RB * nk; idx += T) {
-        const int r2 = idx & (RB - 1), k = idx / RB, row2 = row0 + r2;
-        if (row2 >= ny) continue;
-        const cpx<R>* bb = sm + r2 * RS;
-        const int q = 2 * k + par;
-        const cpx<R> zq = bb[pad16(k)];
-        const cpx<R> zm = par ? bb[pad16(N - 1 - k)] : bb[pad16(k == 0 ? 0 : N - k)];
-        A[Tile<R>::at(row2, q, ldqA)] = mk<R>(R(0.5) * (zq.x + zm.x), R(0.5) * (zq.y - zm.y));
-        if (q <= Q) {
-          const cpx<R> d = mk<R>(zq.x - zm.x, zq.y + zm.y);  // Z(q) - conj Z(M - q)
-          // divided by 2 i (by 2 (-i) in the conjugated pipeline)
-          B[Tile<R>::at(row2, q, ldqB)] = cj ? mk<R>(R(-0.5) * d.y, R(0.5) * d.x)
-                                             : mk<R>(R(0.5) * d.y, R(-0.5) * d.x);
-        }
+      A[Tile<R>::at(row2, q, ldqA)] = mk<R>(R(0.5) * (zq.x + zm.x), R(0.5) * (zq.y - zm.y));
+      if (q <= Q) {
+        const cpx<R> d = mk<R>(zq.x - zm.x, zq.y + zm.y);  // Z(q) - conj Z(M - q)
+        // divided by 2 i (by 2 (-i) in the conjugated pipeline)
+        B[Tile<R>::at(row2, q, ldqB)] = cj ? mk<R>(R(-0.5) * d.y, R(0.5) * d.x)
+                                           : mk<R>(R(0.5) * d.y, R(-0.5) * d.x);
       }
     }
   }
 }
 
+#if DSNU_COL_PAIRED
 // ---------------------------------------------------------------------------
 // Column pass of I1: per column, both chains (even/odd output rows of the
-// padded column DFT) go forward, are multiplied by m1 and come back; the even
-// chain's result is held in shared memory until the odd one is done.  The odd
+// padded column DFT) go forward together, are multiplied by m1 and come back
+// together; their sum is the column of I1's inverse.  All loads of a column
+// precede the first barrier, so the in-place update is safe.
+template <typename R, int LOG2N>
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COLMAIN_MINB))
+k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs<R> mt, int cj) {
+  using GG = Geo<R, LOG2N>;
+  constexpr int G = GG::G, CC = GG::CC, FB = GG::FB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* sm = stw + GG::STWP;
+  copy_to_smem(stw, ay.stw, GG::STW);
+  const int tid = threadIdx.x;
+  const int cl = tid / G, t = tid - cl * G;
+  const R isg = cj ? R(-1) : R(1);
+  cpx<R>* buf_e = sm + (2 * cl) * FB;
+  cpx<R>* buf_o = buf_e + FB;
+  const int items = (ncols + CC - 1) / CC;
+#pragma unroll 1
+  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+    const int mi = it / items, item = it - mi * items;
+    cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(member_at(mem, mi), off.A);
+    const int col = item * CC + cl;
+    const bool valid = col < ncols;
+    const R wx2 = valid ? mt.wx2[col] : R(0);
+    const R gx = valid ? mt.gx[col] : R(0);
+    cpx<R> e[16], o[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int n = t + G * m;
+      const cpx<R> x = valid ? A[Tile<R>::at(n, col, ldqA)] : mk<R>(R(0), R(0));
+      cpx<R> w = twm(ay, n);
+      w.y *= isg;
+      e[m] = x;
+      o[m] = cmul(x, w);
+    }
+    block_fft2_regs<R, LOG2N>(e, o, buf_e, buf_o, t, stw, cj != 0);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int q = 2 * (t + G * m);
+      e[m] = e[m] * (valid ? mult_high(mt, wx2, gx, q) : R(0));
+      o[m] = o[m] * (valid ? mult_high(mt, wx2, gx, q + 1) : R(0));
+    }
+    block_fft2_regs<R, LOG2N>(e, o, buf_e, buf_o, t, stw, cj == 0);
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int n = t + G * m;
+        const cpx<R> w = twm(ay, n);
+        A[Tile<R>::at(n, col, ldqA)] = cj ? e[m] + cmul(o[m], w) : e[m] + cmulc(o[m], w);
+      }
+    }
+  }
+}
+
+#else
+// ---------------------------------------------------------------------------
+// Column pass of I1, one chain at a time: the even chain's result is held in
+// shared memory until the odd one is done (fewer registers than the paired
+// variant).  The odd
 // chain's loads of a column precede its first barrier, so the in-place update
 // is safe.
 template <typename R, int LOG2N>
@@ -309,6 +379,8 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
     }
   }
 }
+
+#endif
 
 // ---------------------------------------------------------------------------
 template <typename R, int LOG2N>
@@ -548,8 +620,9 @@ k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs
 //   T(2j)   = IDFT_N[W(q) + W(q + N)](j)
 //   T(2j+1) = IDFT_N[(W(q) - W(q + N)) e^{+2 pi i q/M}](j),   q < N,
 // with W(q) = Y(q) + i S(q) for q <= N and W(M - q) = conj Y(q) + i conj S(q).
+// Both transforms run together; j < N/2 gives the grid points n < N.
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(Geo<R, LOG2N>::T_RI > 512 ? 1 : DSNU_ROW_MINB))
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(DSNU_ROW_MINB))
 k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
           const R* __restrict__ decon_y, R scale, int cj) {
   using GG = Geo<R, LOG2N>;
@@ -561,7 +634,8 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   const int tid = threadIdx.x;
   const int rr = tid / G, t = tid - rr * G;
   const int si = cj ? -1 : 1;
-  cpx<R>* buf = sm + rr * RS;
+  cpx<R>* buf_u = sm + (2 * rr) * RS;
+  cpx<R>* buf_v = buf_u + RS;
   const int items = (ny + RB - 1) / RB;
 #pragma unroll 1
   for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
@@ -574,49 +648,52 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     const int row = row0 + rr;
     const bool valid = row < ny;
     const R dy = valid ? decon_y[row] : R(0);
-#pragma unroll 1
-    for (int par = 0; par < 2; ++par) {
-      __syncthreads();  // the table copy / previous transform's last-stage loads finished
-      // par 0: U(q) = W(q) + W(q + N); par 1: V(q) = (W(q) - W(q + N)) e^{+2 pi i q/M}
-      for (int idx = tid; idx < RB * N; idx += T) {
-        const int r2 = idx & (RB - 1), q = idx / RB, row2 = row0 + r2;
-        cpx<R> u = mk<R>(R(0), R(0));
-        if (row2 < ny) {
-          cpx<R> y = A[Tile<R>::at(row2, q, ldqA)];
-          cpx<R> s = (q <= Q) ? St[Tile<R>::at(row2, q, ldqB)] : mk<R>(R(0), R(0));
-          const cpx<R> wlo = y + mul_i(s, si);
-          // W(q + N): q = 0 -> W(N) = Y(N) + i S(N); else conj of the mirror N - q
-          const int qm = (q == 0) ? N : N - q;
-          y = A[Tile<R>::at(row2, qm, ldqA)];
-          s = (qm <= Q) ? St[Tile<R>::at(row2, qm, ldqB)] : mk<R>(R(0), R(0));
-          if (q != 0) {
-            y = conj(y);
-            s = conj(s);
-          }
-          const cpx<R> whi = y + mul_i(s, si);
-          if (par == 0) {
-            u = wlo + whi;
-          } else {
-            const cpx<R> w = twm(ax, q);  // e^{-2 pi i q/M}; the inverse uses its conjugate
-            const cpx<R> d = wlo - whi;
-            u = cj ? cmul(d, w) : cmulc(d, w);
-          }
+    __syncthreads();  // the table copy / previous transform's last-stage loads finished
+    // U(q) = W(q) + W(q + N) and V(q) = (W(q) - W(q + N)) e^{+2 pi i q/M}, rows fastest
+    for (int idx = tid; idx < RB * N; idx += T) {
+      const int r2 = idx & (RB - 1), q = idx / RB, row2 = row0 + r2;
+      cpx<R> u = mk<R>(R(0), R(0)), v = mk<R>(R(0), R(0));
+      if (row2 < ny) {
+        cpx<R> y = A[Tile<R>::at(row2, q, ldqA)];
+        cpx<R> s = (q <= Q) ? St[Tile<R>::at(row2, q, ldqB)] : mk<R>(R(0), R(0));
+        const cpx<R> wlo = y + mul_i(s, si);
+        // W(q + N): q = 0 -> W(N) = Y(N) + i S(N); else conj of the mirror N - q
+        const int qm = (q == 0) ? N : N - q;
+        y = A[Tile<R>::at(row2, qm, ldqA)];
+        s = (qm <= Q) ? St[Tile<R>::at(row2, qm, ldqB)] : mk<R>(R(0), R(0));
+        if (q != 0) {
+          y = conj(y);
+          s = conj(s);
         }
-        sm[r2 * RS + pad16(q)] = u;
+        const cpx<R> whi = y + mul_i(s, si);
+        u = wlo + whi;
+        const cpx<R> w = twm(ax, q);  // e^{-2 pi i q/M}; the inverse uses its conjugate
+        const cpx<R> d = wlo - whi;
+        v = cj ? cmul(d, w) : cmulc(d, w);
       }
-      __syncthreads();
-      cpx<R> v[16];
+      cpx<R>* bu = sm + (2 * r2) * RS;
+      bu[pad16(q)] = u;
+      bu[RS + pad16(q)] = v;
+    }
+    __syncthreads();
+    cpx<R> a[16], b[16];
 #pragma unroll
-      for (int m = 0; m < 16; ++m) v[m] = buf[pad16(t + G * m)];
-      block_fft_regs<R, LOG2N>(v, buf, t, stw, cj == 0);
-      if (valid) {
-        // slot m holds T(2 (t + G m) + par); the grid keeps n < N, i.e. m < 8
+    for (int m = 0; m < 16; ++m) {
+      a[m] = buf_u[pad16(t + G * m)];
+      b[m] = buf_v[pad16(t + G * m)];
+    }
+    block_fft2_regs<R, LOG2N>(a, b, buf_u, buf_v, t, stw, cj == 0);
+    if (valid) {
+      // slot m holds T(2 (t + G m)) in a and T(2 (t + G m) + 1) in b; n < N for m < 8
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-          const int n = 2 * (t + G * m) + par;
-          const R im = cj ? -v[m].y : v[m].y;
-          phi[size_t(row) * N + n] = to_f64<R>((v[m].x + im * ax.decon[n] * dy) * scale);
-        }
+      for (int m = 0; m < 8; ++m) {
+        const int n = 2 * (t + G * m);
+        const R ia = cj ? -a[m].y : a[m].y;
+        const R ib = cj ? -b[m].y : b[m].y;
+        double2 out;
+        out.x = to_f64<R>((a[m].x + ia * ax.decon[n] * dy) * scale);
+        out.y = to_f64<R>((b[m].x + ib * ax.decon[n + 1] * dy) * scale);
+        *reinterpret_cast<double2*>(phi + size_t(row) * N + n) = out;
       }
     }
   }
