@@ -433,6 +433,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "n": n, "L": L, "P": WL["P"], "n_r": WL["n_r"],
                    "n_theta": WL["n_theta"], "kernel_width": info.kernel_width, "band_q": info.band_q,
+                   "spread_tile_split_chunk": [info.spread_tile, info.spread_split, info.spread_chunk],
                    "global_batch": world, "parallelism": f"independent solves x{world}",
                    "l2": f"inputs larger than L2: {N_ROT} rotating 134 MB input/output pairs"},
         "fp64": {"value": value64, "unit": "solves/s", "ms_per_step": t64 * 1000.0 / k64, "steps": k64,

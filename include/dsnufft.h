@@ -86,6 +86,9 @@ typedef struct dsnu_plan_s* dsnu_plan;
  * deconvolution and multiplier tables and the twiddle tables, bins the nodes
  * into spreading tiles, and uploads the tables with cudaMemcpyAsync on
  * `stream` (cudaStream_t, may be NULL), then synchronises that stream.
+ * The spreading tile configuration is chosen by timing the candidates on the
+ * device (temporary scratch, cached per device and parameters for the
+ * process); DSNU_AUTOTUNE=0 in the environment keeps the default one.
  * Ownership: the plan owns its tables (device memory, freed by
  * dsnu_plan_destroy); it does not own the workspace.
  * Errors: DSNU_EINVAL (bad params, *out untouched), DSNU_ENOMEM, DSNU_ECUDA. */
@@ -284,7 +287,9 @@ typedef struct {
   int32_t n_tiles;       /* spreading tiles */
   int32_t max_tile_nodes;
   int32_t n_items;       /* spreading work items (tiles cut into pieces) */
-  int32_t reserved;
+  int32_t spread_tile;   /* spreading configuration chosen at plan creation: */
+  int32_t spread_split;  /*   tile edge (cells), threads per cell, entries per item */
+  int32_t spread_chunk;
 } dsnu_plan_info;
 
 dsnu_status dsnu_plan_get_info(dsnu_plan plan, dsnu_plan_info* info);

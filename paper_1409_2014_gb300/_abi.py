@@ -49,7 +49,8 @@ class dsnu_plan_info(ctypes.Structure):
         ("kernel_width", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("sigma", ctypes.c_double), ("es_beta", ctypes.c_double),
         ("n_tiles", ctypes.c_int32), ("max_tile_nodes", ctypes.c_int32),
-        ("n_items", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("n_items", ctypes.c_int32), ("spread_tile", ctypes.c_int32),
+        ("spread_split", ctypes.c_int32), ("spread_chunk", ctypes.c_int32),
     ]
 
 

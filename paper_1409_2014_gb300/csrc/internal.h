@@ -67,6 +67,8 @@ struct PlanGeom {
   double dky2;             // dk_y^2
   int cap_rowf, cap_col, cap_bandf, cap_bandi, cap_rowi;  // resident CTAs (SMs x occupancy)
   int w, Q, n_nodes, n_tiles, tiles_x, tiles_y, max_tile_nodes, n_items;
+  int spread_cfg;          // index into kSpreadCfgs (chosen by the autotuner)
+  int spread_tile;         // its tile edge (cells)
   int precision, sharp;
   double beta, sigma, cut_radius;
   double scale;  // 1/(Mx My)
@@ -79,6 +81,12 @@ constexpr int kProfEvents = kStages + 1;  // events per profiled solve (see run_
 // holds kProfEvents events recorded around the kernels.
 dsnu_status run_pipeline_f32(const PlanGeom& g, const PlanTables& t, const WsLayout& L,
                              const Members& mem, cudaStream_t st, int cj, cudaEvent_t* ev);
+// Time one spreading configuration (spread + reduce, `reps` launches) on
+// scratch buffers laid out by L; returns the average milliseconds in *ms.
+cudaError_t time_spread_f32(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws, int reps,
+                            float* ms);
+cudaError_t time_spread_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws, int reps,
+                            float* ms);
 dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L,
                              const Members& mem, cudaStream_t st, int cj, cudaEvent_t* ev);
 
@@ -105,7 +113,8 @@ struct dsnu_plan_s {
   dsnu::PlanGeom geom;
   dsnu::PlanTables tab;
   dsnu::WsLayout ws_layout;
-  void* table_block;        // one device allocation holding every table
+  void* table_block;        // one device allocation holding every table but the spreading ones
+  void* spread_block;       // spreading tables of the chosen tile configuration
   size_t table_bytes;
   void* ws;                 // caller-owned workspace
   size_t ws_bytes;

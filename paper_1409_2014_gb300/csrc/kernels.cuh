@@ -475,52 +475,55 @@ k_interp(Members mem, WsOff off, int ldq, int Q, const int2* __restrict__ q0,
 }
 
 // ---------------------------------------------------------------------------
-// Type-1 spreading as a gather over 8 x 8 tiles of band cells.  At plan time
-// the (node, stencil origin, ES weights) entries of every node whose stencil
-// meets a tile are laid out contiguously per tile and cut into work items of
-// at most kSpreadChunk entries.  k_spread: one CTA per work item; each cell is
-// served by kSplit threads that take every kSplit-th entry; the CTA writes the
-// item's partial sums.  k_spread_reduce: per tile, adds its items' partial
+// Type-1 spreading as a gather over TILE x TILE tiles of band cells.  At plan
+// time the (node, stencil origin, ES weights) entries of every node whose
+// stencil meets a tile are laid out contiguously per tile and cut into work
+// items of at most CHUNK entries.  k_spread: one CTA per work item; each cell
+// is served by SPLIT threads that take every SPLIT-th entry; the CTA writes
+// the item's partial sums.  k_spread_reduce: per tile, adds its items' partial
 // sums in item order (deterministic, no atomics) and applies the centring
-// phase.
-constexpr int kTile = 8;
-constexpr int kSplit = 4;
-constexpr int kSpreadThreads = kTile * kTile * kSplit;
-constexpr int kSpreadChunk = 128;
+// phase.  The (TILE, SPLIT, CHUNK) configuration is chosen per plan by timing
+// the candidates below (see autotune_spread in plan.cu).
+struct SpreadCfg {
+  int tile, split, chunk;
+};
+constexpr int kNumSpreadCfgs = 4;
+constexpr SpreadCfg kSpreadCfgs[kNumSpreadCfgs] = {{8, 4, 128}, {8, 2, 128}, {16, 1, 128}, {16, 2, 64}};
 
-template <typename R>
-__global__ void __launch_bounds__(kSpreadThreads)
+template <typename R, int TILE, int SPLIT, int CHUNK>
+__global__ void __launch_bounds__(TILE * TILE * SPLIT)
 k_spread(Members mem, WsOff off, const int2* __restrict__ item_range,
          const int* __restrict__ ent_node, const int2* __restrict__ ent_q0,
          const R* __restrict__ ent_w, const int* __restrict__ item_tile, int w, int tiles_x, int Q) {
+  constexpr int CELLS = TILE * TILE, THREADS = CELLS * SPLIT;
+  __shared__ int2 s_q0[CHUNK];
+  __shared__ cpx<R> s_c[CHUNK];
+  __shared__ R s_w[CHUNK * 32];
+  __shared__ R s_red[2][SPLIT][CELLS];
   const Member mb = member_at(mem, blockIdx.y);
   const cpx<R>* __restrict__ c = ws_ptr<cpx<R>>(mb, off.c);
   cpx<R>* __restrict__ partial = ws_ptr<cpx<R>>(mb, off.partial);
-  __shared__ int2 s_q0[kSpreadChunk];
-  __shared__ cpx<R> s_c[kSpreadChunk];
-  __shared__ R s_w[kSpreadChunk * 32];
-  __shared__ R s_red[2][kSplit][kTile * kTile];
   const int item = blockIdx.x;
   const int tile = item_tile[item];
   const int tx = tile % tiles_x, ty = tile / tiles_x;
-  const int cell = threadIdx.x & (kTile * kTile - 1), part = threadIdx.x / (kTile * kTile);
-  const int qx = tx * kTile + (cell & (kTile - 1));
-  const int qy = ty * kTile + (cell / kTile) - Q;
+  const int cell = threadIdx.x & (CELLS - 1), part = threadIdx.x / CELLS;
+  const int qx = tx * TILE + (cell & (TILE - 1));
+  const int qy = ty * TILE + (cell / TILE) - Q;
   const int2 rg = item_range[item];
-  const int s0 = rg.x, cnt = rg.y - rg.x;  // cnt <= kSpreadChunk
+  const int s0 = rg.x, cnt = rg.y - rg.x;  // cnt <= CHUNK
   const int w2 = 2 * w;
-  for (int i = threadIdx.x; i < cnt; i += kSpreadThreads) {
+  for (int i = threadIdx.x; i < cnt; i += THREADS) {
     s_q0[i] = ent_q0[s0 + i];
     s_c[i] = c[ent_node[s0 + i]];
   }
   const R* src = ent_w + size_t(s0) * w2;
-  for (int i = threadIdx.x; i < cnt * w2; i += kSpreadThreads) {
+  for (int i = threadIdx.x; i < cnt * w2; i += THREADS) {
     const int e = i / w2;
     s_w[e * 32 + (i - e * w2)] = src[i];
   }
   __syncthreads();
   R ax = R(0), ay = R(0);
-  for (int k = part; k < cnt; k += kSplit) {
+  for (int k = part; k < cnt; k += SPLIT) {
     const int a = qx - s_q0[k].x, b = qy - s_q0[k].y;
     if ((unsigned)a < (unsigned)w && (unsigned)b < (unsigned)w) {
       const R f = s_w[k * 32 + a] * s_w[k * 32 + w + b];
@@ -528,23 +531,25 @@ k_spread(Members mem, WsOff off, const int2* __restrict__ item_range,
       ay += f * s_c[k].y;
     }
   }
-  s_red[0][part][cell] = ax;
-  s_red[1][part][cell] = ay;
-  __syncthreads();
-  if (part == 0) {
+  if constexpr (SPLIT > 1) {
+    s_red[0][part][cell] = ax;
+    s_red[1][part][cell] = ay;
+    __syncthreads();
+    if (part != 0) return;
 #pragma unroll
-    for (int p = 1; p < kSplit; ++p) {
+    for (int p = 1; p < SPLIT; ++p) {
       ax += s_red[0][p][cell];
       ay += s_red[1][p][cell];
     }
-    partial[size_t(item) * (kTile * kTile) + cell] = mk<R>(ax, ay);
   }
+  partial[size_t(item) * CELLS + cell] = mk<R>(ax, ay);
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kTile * kTile)
+template <typename R, int TILE>
+__global__ void __launch_bounds__(TILE * TILE)
 k_spread_reduce(Members mem, WsOff off, const int* __restrict__ tile_items, int tiles_x,
                 int n_tiles, int Q, int ldq, int cj) {
+  constexpr int CELLS = TILE * TILE;
   const Member mb = member_at(mem, blockIdx.y);
   const cpx<R>* __restrict__ partial = ws_ptr<cpx<R>>(mb, off.partial);
   cpx<R>* __restrict__ Sband = ws_ptr<cpx<R>>(mb, off.Sband);
@@ -552,11 +557,11 @@ k_spread_reduce(Members mem, WsOff off, const int* __restrict__ tile_items, int 
   if (tile >= n_tiles) return;
   const int cell = threadIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
-  const int qx = tx * kTile + (cell & (kTile - 1));
-  const int qy = ty * kTile + (cell / kTile) - Q;
+  const int qx = tx * TILE + (cell & (TILE - 1));
+  const int qy = ty * TILE + (cell / TILE) - Q;
   R ax = R(0), ay = R(0);
   for (int it = tile_items[tile]; it < tile_items[tile + 1]; ++it) {
-    const cpx<R> v = partial[size_t(it) * (kTile * kTile) + cell];
+    const cpx<R> v = partial[size_t(it) * CELLS + cell];
     ax += v.x;
     ay += v.y;
   }
@@ -564,6 +569,29 @@ k_spread_reduce(Members mem, WsOff off, const int* __restrict__ tile_items, int 
     const int e = qx + qy;
     Sband[size_t(qx) * ldq + qy + Q] = mul_ipow(mk<R>(ax, ay), cj ? e : -e);  // (-i)^{q_x+q_y}
   }
+}
+
+// Launch the spreading pair with configuration `cfg`: part 0 = k_spread,
+// part 1 = k_spread_reduce, part 2 = both.
+template <typename R>
+void launch_spread(int cfg, const Members& mem, const WsOff& off, const PlanTables& t, const PlanGeom& g,
+                   int ldq, int cj, cudaStream_t st, int part) {
+  const R* ew = static_cast<const R*>(t.ent_w);
+#define DSNU_SPREAD(TL, SP, CH)                                                                     \
+  if (part != 1 && g.n_items > 0)                                                                 \
+    k_spread<R, TL, SP, CH><<<dim3(g.n_items, mem.count), TL * TL * SP, 0, st>>>(                   \
+        mem, off, t.item_range, t.ent_node, t.ent_q0, ew, t.item_tile, g.w, g.tiles_x, g.Q);         \
+  if (part != 0)                                                                                    \
+    k_spread_reduce<R, TL><<<dim3(g.n_tiles, mem.count), TL * TL, 0, st>>>(mem, off, t.tile_items,  \
+                                                                          g.tiles_x, g.n_tiles, g.Q, \
+                                                                          ldq, cj)
+  switch (cfg) {
+    case 1: DSNU_SPREAD(8, 2, 128); break;
+    case 2: DSNU_SPREAD(16, 1, 128); break;
+    case 3: DSNU_SPREAD(16, 2, 64); break;
+    default: DSNU_SPREAD(8, 4, 128); break;
+  }
+#undef DSNU_SPREAD
 }
 
 // ---------------------------------------------------------------------------

@@ -140,13 +140,9 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
   k_interp<R><<<dim3((g.n_nodes + 7) / 8, mem.count), 256, 0, st>>>(mem, off, L.ldq, g.Q, t.node_q0, wts,
                                                                      t.node_D, g.n_nodes, g.w, cj);
   DSNU_MARK(3);
-  if (g.n_items > 0)
-    k_spread<R><<<dim3(g.n_items, mem.count), kSpreadThreads, 0, st>>>(
-        mem, off, t.item_range, t.ent_node, t.ent_q0, static_cast<const R*>(t.ent_w), t.item_tile, g.w,
-        g.tiles_x, g.Q);
+  launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, cj, st, 0);
   DSNU_MARK(4);
-  k_spread_reduce<R><<<dim3(g.n_tiles, mem.count), kTile * kTile, 0, st>>>(mem, off, t.tile_items, g.tiles_x,
-                                                                            g.n_tiles, g.Q, L.ldq, cj);
+  launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, cj, st, 1);
   DSNU_MARK(5);
   switch (g.log2ny) {
     DSNU_LOG2_CASES(DSNU_BANDI)
@@ -175,6 +171,28 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
     return DSNU_ECUDA;
   }
   return DSNU_OK;
+}
+
+template <typename R>
+cudaError_t time_spread(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws, int reps, float* ms) {
+  const WsOff off{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial};
+  const Members mem = single_member(nullptr, nullptr, ws);
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return e;
+  launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, 0, 0, 2);  // warm-up
+  cudaEventRecord(e0, 0);
+  for (int i = 0; i < reps; ++i) launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, 0, 0, 2);
+  cudaEventRecord(e1, 0);
+  e = cudaEventSynchronize(e1);
+  float total = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&total, e0, e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  *ms = total / float(reps);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return e;
 }
 
 }  // namespace dsnu

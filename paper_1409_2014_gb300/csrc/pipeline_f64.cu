@@ -7,4 +7,8 @@ dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLay
   return run_pipeline<double>(g, t, L, mem, st, cj, ev);
 }
 cudaError_t prepare_kernels_f64(PlanGeom& g) { return prepare_kernels<double>(g); }
+cudaError_t time_spread_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws, int reps,
+                            float* ms) {
+  return time_spread<double>(g, t, L, ws, reps, ms);
+}
 }  // namespace dsnu

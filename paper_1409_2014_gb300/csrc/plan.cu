@@ -19,7 +19,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -120,11 +123,66 @@ struct HostTables {
   std::vector<int2> node_q0;
   std::vector<R> node_w;
   std::vector<double> node_D;
-  std::vector<int> tile_ptr, ent_node, tile_items, item_tile;
-  std::vector<int2> item_range;
-  std::vector<int2> ent_q0;
-  std::vector<R> ent_w;
 };
+
+// Spreading tables for one tile configuration (see k_spread).
+template <typename R>
+struct HostSpread {
+  std::vector<int> tile_ptr, ent_node, tile_items, item_tile;
+  std::vector<int2> ent_q0, item_range;
+  std::vector<R> ent_w;
+  int tiles_x = 0, tiles_y = 0, n_tiles = 0, n_items = 0, max_tile = 0;
+};
+
+// Bin the nodes into cfg.tile x cfg.tile tiles of band cells over q_x in
+// [0, Q], q_y in [-Q, Q]; per tile, the entries of every node whose stencil
+// meets it, cut into work items of at most cfg.chunk entries.
+template <typename R>
+static void bin_spread(const std::vector<int2>& q0, const std::vector<R>& nw, int w, int Q, const SpreadCfg& cfg,
+                       HostSpread<R>& H) {
+  const int TS = cfg.tile, nn = int(q0.size());
+  H.tiles_x = (Q + 1 + TS - 1) / TS;
+  H.tiles_y = (2 * Q + 1 + TS - 1) / TS;
+  H.n_tiles = H.tiles_x * H.tiles_y;
+  std::vector<std::vector<int>> lists(H.n_tiles);
+  for (int j = 0; j < nn; ++j) {
+    const int xlo = std::max(q0[j].x, 0), xhi = std::min(q0[j].x + w - 1, Q);
+    if (xhi < xlo) continue;
+    const int ylo = q0[j].y + Q, yhi = q0[j].y + w - 1 + Q;
+    for (int ty = ylo / TS; ty <= yhi / TS; ++ty)
+      for (int tx = xlo / TS; tx <= xhi / TS; ++tx) lists[ty * H.tiles_x + tx].push_back(j);
+  }
+  H.tile_ptr.assign(H.n_tiles + 1, 0);
+  H.max_tile = 0;
+  for (int i = 0; i < H.n_tiles; ++i) {
+    H.tile_ptr[i + 1] = H.tile_ptr[i] + int(lists[i].size());
+    H.max_tile = std::max(H.max_tile, int(lists[i].size()));
+  }
+  for (auto& l : lists)
+    for (int j : l) {
+      H.ent_node.push_back(j);
+      H.ent_q0.push_back(q0[j]);
+      H.ent_w.insert(H.ent_w.end(), nw.begin() + size_t(j) * 2 * w, nw.begin() + size_t(j + 1) * 2 * w);
+    }
+  if (H.ent_node.empty()) {
+    H.ent_node.push_back(0);
+    H.ent_q0.push_back(make_int2(0, 0));
+    H.ent_w.resize(2 * w, R(0));
+  }
+  H.tile_items.assign(H.n_tiles + 1, 0);
+  for (int i = 0; i < H.n_tiles; ++i) {
+    for (int b = H.tile_ptr[i]; b < H.tile_ptr[i + 1]; b += cfg.chunk) {
+      H.item_range.push_back(make_int2(b, std::min(b + cfg.chunk, H.tile_ptr[i + 1])));
+      H.item_tile.push_back(i);
+    }
+    H.tile_items[i + 1] = int(H.item_range.size());
+  }
+  H.n_items = int(H.item_range.size());
+  if (H.item_range.empty()) {
+    H.item_range.push_back(make_int2(0, 0));
+    H.item_tile.push_back(0);
+  }
+}
 
 static void twiddles(int n, int m, std::vector<double>& out) {
   out.resize(2 * n);
@@ -187,6 +245,110 @@ struct Builder {
   template <typename T>
   size_t add(const std::vector<T>& v) { return add(v.data(), v.size() * sizeof(T)); }
 };
+
+
+template <typename R>
+static dsnu_status upload_spread(const HostSpread<R>& H, cudaStream_t st, void** block, PlanTables& t) {
+  Builder b;
+  const size_t o_ti = b.add(H.tile_items), o_ir = b.add(H.item_range), o_it = b.add(H.item_tile);
+  const size_t o_en = b.add(H.ent_node), o_eq = b.add(H.ent_q0), o_ew = b.add(H.ent_w);
+  void* dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, b.bytes.size());
+  if (e != cudaSuccess) return fail(DSNU_ENOMEM, std::string("cudaMalloc(spread tables): ") + cudaGetErrorString(e));
+  e = cudaMemcpyAsync(dev, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    return fail(DSNU_ECUDA, std::string("spread table upload: ") + cudaGetErrorString(e));
+  }
+  char* d = static_cast<char*>(dev);
+  t.tile_items = reinterpret_cast<int*>(d + o_ti);
+  t.item_range = reinterpret_cast<int2*>(d + o_ir);
+  t.item_tile = reinterpret_cast<int*>(d + o_it);
+  t.ent_node = reinterpret_cast<int*>(d + o_en);
+  t.ent_q0 = reinterpret_cast<int2*>(d + o_eq);
+  t.ent_w = d + o_ew;
+  *block = dev;
+  return DSNU_OK;
+}
+
+static void set_spread_geom(PlanGeom& g, int cfg, int tiles_x, int tiles_y, int n_items, int max_tile) {
+  g.spread_cfg = cfg;
+  g.spread_tile = kSpreadCfgs[cfg].tile;
+  g.tiles_x = tiles_x;
+  g.tiles_y = tiles_y;
+  g.n_tiles = tiles_x * tiles_y;
+  g.n_items = n_items;
+  g.max_tile_nodes = max_tile;
+}
+
+static void layout_workspace(dsnu_plan_s* P);
+
+static std::mutex g_tune_mutex;
+static std::map<std::string, int> g_tune_cache;
+
+// Choose the spreading configuration: DSNU_AUTOTUNE=0 in the environment
+// keeps the first candidate; otherwise every candidate of kSpreadCfgs is
+// timed on scratch buffers (values do not change its cost) and the fastest is
+// kept, cached per device and plan geometry for the process.
+template <typename R>
+static dsnu_status setup_spread(dsnu_plan_s* P, const std::vector<int2>& q0, const std::vector<R>& nw,
+                                cudaStream_t st) {
+  PlanGeom& g = P->geom;
+  const dsnu_params& p = P->prm;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  char key[256];
+  std::snprintf(key, sizeof(key), "%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|%d|%d", dev, p.nx, p.ny, p.lx, p.ly,
+                p.cut_radius, p.sigma, p.n_r, p.n_theta, p.kernel_width, p.precision, p.partition);
+  const char* env = std::getenv("DSNU_AUTOTUNE");
+  const bool tune = !(env && env[0] == '0');
+  int choice = 0;
+  bool have = !tune;
+  if (tune) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      choice = it->second;
+      have = true;
+    }
+  }
+  if (!have) {
+    float best = 1e30f;
+    for (int c = 0; c < kNumSpreadCfgs; ++c) {
+      HostSpread<R> H;
+      bin_spread<R>(q0, nw, g.w, g.Q, kSpreadCfgs[c], H);
+      void* blk = nullptr;
+      PlanTables t = P->tab;
+      dsnu_status s = upload_spread<R>(H, st, &blk, t);
+      if (s != DSNU_OK) return s;
+      set_spread_geom(g, c, H.tiles_x, H.tiles_y, H.n_items, H.max_tile);
+      layout_workspace(P);
+      void* ws = nullptr;
+      cudaError_t e = cudaMalloc(&ws, P->ws_layout.total);
+      if (e == cudaSuccess) e = cudaMemset(ws, 0, P->ws_layout.total);
+      float ms = 0.f;
+      if (e == cudaSuccess)
+        e = (g.precision == DSNU_MIXED) ? time_spread_f32(g, t, P->ws_layout, ws, 5, &ms)
+                                        : time_spread_f64(g, t, P->ws_layout, ws, 5, &ms);
+      if (ws) cudaFree(ws);
+      cudaFree(blk);
+      if (e != cudaSuccess) return fail(DSNU_ECUDA, std::string("spread autotune: ") + cudaGetErrorString(e));
+      if (ms < best) {
+        best = ms;
+        choice = c;
+      }
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = choice;
+  }
+  HostSpread<R> H;
+  bin_spread<R>(q0, nw, g.w, g.Q, kSpreadCfgs[choice], H);
+  const dsnu_status s = upload_spread<R>(H, st, &P->spread_block, P->tab);
+  if (s != DSNU_OK) return s;
+  set_spread_geom(g, choice, H.tiles_x, H.tiles_y, H.n_items, H.max_tile);
+  return DSNU_OK;
+}
 
 template <typename R>
 static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
@@ -278,57 +440,6 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
     return fail(DSNU_EINVAL, "disk plus ES stencil does not fit the padded grid: need P*h + w*pi/M < pi");
   g.Q = Q;
 
-  // spreading tiles (kTile x kTile cells) over q_x in [0, Q], q_y in [-Q, Q];
-  // per tile, the entries of every node whose stencil meets it
-  const int TS = kTile;
-  g.tiles_x = (Q + 1 + TS - 1) / TS;
-  g.tiles_y = (2 * Q + 1 + TS - 1) / TS;
-  g.n_tiles = g.tiles_x * g.tiles_y;
-  std::vector<std::vector<int>> lists(g.n_tiles);
-  for (int j = 0; j < nn; ++j) {
-    const int xlo = std::max(T.node_q0[j].x, 0), xhi = std::min(T.node_q0[j].x + w - 1, Q);
-    if (xhi < xlo) continue;
-    const int ylo = T.node_q0[j].y + Q, yhi = T.node_q0[j].y + w - 1 + Q;
-    for (int ty = ylo / TS; ty <= yhi / TS; ++ty)
-      for (int tx = xlo / TS; tx <= xhi / TS; ++tx) lists[ty * g.tiles_x + tx].push_back(j);
-  }
-  T.tile_ptr.assign(g.n_tiles + 1, 0);
-  g.max_tile_nodes = 0;
-  for (int i = 0; i < g.n_tiles; ++i) {
-    T.tile_ptr[i + 1] = T.tile_ptr[i] + int(lists[i].size());
-    g.max_tile_nodes = std::max(g.max_tile_nodes, int(lists[i].size()));
-  }
-  const size_t n_ent = size_t(T.tile_ptr.back());
-  T.ent_node.reserve(n_ent + 1);
-  T.ent_q0.reserve(n_ent + 1);
-  T.ent_w.reserve((n_ent + 1) * 2 * w);
-  for (auto& l : lists)
-    for (int j : l) {
-      T.ent_node.push_back(j);
-      T.ent_q0.push_back(T.node_q0[j]);
-      T.ent_w.insert(T.ent_w.end(), T.node_w.begin() + size_t(j) * 2 * w,
-                     T.node_w.begin() + size_t(j + 1) * 2 * w);
-    }
-  if (T.ent_node.empty()) {
-    T.ent_node.push_back(0);
-    T.ent_q0.push_back(make_int2(0, 0));
-    T.ent_w.resize(2 * w, R(0));
-  }
-  // work items: each tile's entries cut into pieces of at most kSpreadChunk
-  T.tile_items.assign(g.n_tiles + 1, 0);
-  for (int i = 0; i < g.n_tiles; ++i) {
-    for (int b = T.tile_ptr[i]; b < T.tile_ptr[i + 1]; b += kSpreadChunk) {
-      T.item_range.push_back(make_int2(b, std::min(b + kSpreadChunk, T.tile_ptr[i + 1])));
-      T.item_tile.push_back(i);
-    }
-    T.tile_items[i + 1] = int(T.item_range.size());
-  }
-  g.n_items = int(T.item_range.size());
-  if (T.item_range.empty()) {
-    T.item_range.push_back(make_int2(0, 0));
-    T.item_tile.push_back(0);
-  }
-
   // one device block for every table
   Builder b;
   const size_t o_stx = b.add(T.stw_x), o_tlx = b.add(T.twm_lo_x), o_thx = b.add(T.twm_hi_x);
@@ -337,9 +448,6 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   const size_t o_dy = b.add(T.decon_y);
   const size_t o_wx2 = b.add(T.m_wx2), o_gx = b.add(T.m_gx), o_gy = b.add(T.m_gy);
   const size_t o_q0 = b.add(T.node_q0), o_w = b.add(T.node_w), o_D = b.add(T.node_D);
-  const size_t o_ti = b.add(T.tile_items), o_ir = b.add(T.item_range), o_it = b.add(T.item_tile);
-  const size_t o_en = b.add(T.ent_node), o_eq = b.add(T.ent_q0);
-  const size_t o_ew = b.add(T.ent_w);
   const int zero = 0;
   const size_t o_st = b.add(&zero, sizeof(int));
   void* dev = nullptr;
@@ -359,19 +467,13 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   t.node_q0 = reinterpret_cast<int2*>(d + o_q0);
   t.node_w = d + o_w;
   t.node_D = reinterpret_cast<double*>(d + o_D);
-  t.tile_items = reinterpret_cast<int*>(d + o_ti);
-  t.item_range = reinterpret_cast<int2*>(d + o_ir);
-  t.item_tile = reinterpret_cast<int*>(d + o_it);
-  t.ent_node = reinterpret_cast<int*>(d + o_en);
-  t.ent_q0 = reinterpret_cast<int2*>(d + o_eq);
-  t.ent_w = d + o_ew;
   t.status = reinterpret_cast<int*>(d + o_st);
   P->table_block = dev;
   P->table_bytes = b.bytes.size();
-  return DSNU_OK;
+  return setup_spread<R>(P, T.node_q0, T.node_w, st);
 }
 
-static void layout_workspace(dsnu_plan_s* P) {
+static void layout_workspace(dsnu_plan_s* P) {  // defined after the autotuner, which uses it
   const PlanGeom& g = P->geom;
   const size_t csz = (g.precision == DSNU_MIXED) ? 8 : 16;
   WsLayout& L = P->ws_layout;
@@ -389,7 +491,7 @@ static void layout_workspace(dsnu_plan_s* P) {
   L.off_Bband = take(size_t(g.Q + 1) * L.ldq * csz);
   L.off_Sband = take(size_t(g.Q + 1) * L.ldq * csz);
   L.off_c = take(size_t(g.n_nodes) * csz);
-  L.off_partial = take(size_t(std::max(g.n_items, 1)) * kTile * kTile * csz);
+  L.off_partial = take(size_t(std::max(g.n_items, 1)) * g.spread_tile * g.spread_tile * csz);
   L.total = off;
 }
 
@@ -443,11 +545,14 @@ dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan*
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   dsnu_status s = (p.precision == DSNU_MIXED) ? build_tables<float>(P, st) : build_tables<double>(P, st);
   if (s != DSNU_OK) {
+    if (P->spread_block) cudaFree(P->spread_block);
+    if (P->table_block) cudaFree(P->table_block);
     delete P;
     return s;
   }
   const cudaError_t e = (p.precision == DSNU_MIXED) ? prepare_kernels_f32(g) : prepare_kernels_f64(g);
   if (e != cudaSuccess) {
+    if (P->spread_block) cudaFree(P->spread_block);
     cudaFree(P->table_block);
     delete P;
     return fail(DSNU_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
@@ -517,6 +622,7 @@ dsnu_status dsnu_status_poll(dsnu_plan plan, void* stream) {
 dsnu_status dsnu_plan_destroy(dsnu_plan plan) {
   if (!plan) return DSNU_OK;
   free_profile(plan);
+  if (plan->spread_block) cudaFree(plan->spread_block);
   cudaError_t e = cudaFree(plan->table_block);
   delete plan;
   if (e != cudaSuccess) return fail(DSNU_ECUDA, std::string("cudaFree: ") + cudaGetErrorString(e));
@@ -600,7 +706,9 @@ dsnu_status dsnu_plan_get_info(dsnu_plan plan, dsnu_plan_info* info) {
   info->n_tiles = g.n_tiles;
   info->max_tile_nodes = g.max_tile_nodes;
   info->n_items = g.n_items;
-  info->reserved = 0;
+  info->spread_tile = g.spread_tile;
+  info->spread_split = kSpreadCfgs[g.spread_cfg].split;
+  info->spread_chunk = kSpreadCfgs[g.spread_cfg].chunk;
   return DSNU_OK;
 }
 

@@ -42,7 +42,7 @@ def test_struct_layout_matches_header():
     assert _abi.dsnu_params.lx.offset == 8
     assert _abi.dsnu_params.n_r.offset == 40
     assert _abi.dsnu_params.partition.offset == 60
-    assert ctypes.sizeof(_abi.dsnu_plan_info) == 48
+    assert ctypes.sizeof(_abi.dsnu_plan_info) == 56
 
 
 def _params(**kw):

@@ -189,3 +189,29 @@ def test_profile_reports_every_stage():
     assert cnt == 3 and len(stages) == dsnu_stage_count() == 8
     assert all(v > 0 for v in stages.values())
     plan.close()
+
+
+def test_spread_autotune_choice_is_reported_and_results_agree():
+    """Every spreading configuration gives the same potential to rounding; the
+    autotuned plan reports one of the candidates."""
+    import os
+
+    from paper_1409_2014_gb300 import Plan
+
+    n, L = 256, 16.0
+    rho = torch.from_numpy(synth.density_sum(n, n, L, L, seed=6, count=5)).cuda()
+    plan = Plan(n, lx=L, cut_radius=6.0, n_r=32, n_theta=64, precision="fp64")
+    info = plan.info
+    assert (info.spread_tile, info.spread_split, info.spread_chunk) in {(8, 4, 128), (8, 2, 128), (16, 1, 128),
+                                                                        (16, 2, 64)}
+    ref = plan.solve(rho).cpu().numpy()
+    plan.close()
+    os.environ["DSNU_AUTOTUNE"] = "0"
+    try:
+        plan0 = Plan(n, lx=L, cut_radius=6.0, n_r=32, n_theta=64, precision="fp64")
+    finally:
+        del os.environ["DSNU_AUTOTUNE"]
+    assert (plan0.info.spread_tile, plan0.info.spread_split) == (8, 4)
+    got = plan0.solve(rho).cpu().numpy()
+    plan0.close()
+    assert np.abs(got - ref).max() <= 1e-14 * np.abs(ref).max()
