@@ -103,11 +103,18 @@ __device__ __forceinline__ void dft_rec(cpx<R> (&v)[RAD]) {
     dft_rec<H, R>(o);
     constexpr int step = 16 / RAD;
     // twiddle o[k] by e^{-2 pi i k/RAD} = rot16<k*step>
+    // (for the factor -i the sum and difference are written out: no multiply)
 #define DSNU_TW(K)                                                         \
   if constexpr ((K) < H) {                                                 \
-    cpx<R> t = rot16<((K) * step) & 15, R>(o[(K)]);                        \
-    v[(K)] = e[(K)] + t;                                                   \
-    v[(K) + H] = e[(K)] - t;                                               \
+    constexpr int RK = ((K) * step) & 15;                                  \
+    if constexpr (RK == 4) {                                               \
+      v[(K)] = mk<R>(e[(K)].x + o[(K)].y, e[(K)].y - o[(K)].x);            \
+      v[(K) + H] = mk<R>(e[(K)].x - o[(K)].y, e[(K)].y + o[(K)].x);        \
+    } else {                                                               \
+      cpx<R> t = rot16<RK, R>(o[(K)]);                                     \
+      v[(K)] = e[(K)] + t;                                                 \
+      v[(K) + H] = e[(K)] - t;                                             \
+    }                                                                      \
   }
     DSNU_TW(0) DSNU_TW(1) DSNU_TW(2) DSNU_TW(3) DSNU_TW(4) DSNU_TW(5) DSNU_TW(6) DSNU_TW(7)
 #undef DSNU_TW

@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(DSNU_ROW_MI
 k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
           const R* __restrict__ decon_y, R scale, int cj) {
   using GG = Geo<R, LOG2N>;
-  constexpr int N = GG::N, G = GG::G, RB = GG::RB_I, T = GG::T_RI, RS = GG::RS;
+  constexpr int N = GG::N, G = GG::G, RB = GG::RB_I, RS = GG::RS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* sm = stw + GG::STWP;
@@ -676,39 +676,48 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     const int row = row0 + rr;
     const bool valid = row < ny;
     const R dy = valid ? decon_y[row] : R(0);
-    __syncthreads();  // the table copy / previous transform's last-stage loads finished
-    // U(q) = W(q) + W(q + N) and V(q) = (W(q) - W(q + N)) e^{+2 pi i q/M}, rows fastest
-    for (int idx = tid; idx < RB * N; idx += T) {
-      const int r2 = idx & (RB - 1), q = idx / RB, row2 = row0 + r2;
-      cpx<R> u = mk<R>(R(0), R(0)), v = mk<R>(R(0), R(0));
-      if (row2 < ny) {
-        cpx<R> y = A[Tile<R>::at(row2, q, ldqA)];
-        cpx<R> s = (q <= Q) ? St[Tile<R>::at(row2, q, ldqB)] : mk<R>(R(0), R(0));
-        const cpx<R> wlo = y + mul_i(s, si);
-        // W(q + N): q = 0 -> W(N) = Y(N) + i S(N); else conj of the mirror N - q
-        const int qm = (q == 0) ? N : N - q;
-        y = A[Tile<R>::at(row2, qm, ldqA)];
-        s = (qm <= Q) ? St[Tile<R>::at(row2, qm, ldqB)] : mk<R>(R(0), R(0));
-        if (q != 0) {
-          y = conj(y);
-          s = conj(s);
-        }
-        const cpx<R> whi = y + mul_i(s, si);
-        u = wlo + whi;
-        const cpx<R> w = twm(ax, q);  // e^{-2 pi i q/M}; the inverse uses its conjugate
-        const cpx<R> d = wlo - whi;
-        v = cj ? cmul(d, w) : cmulc(d, w);
-      }
-      cpx<R>* bu = sm + (2 * r2) * RS;
-      bu[pad16(q)] = u;
-      bu[RS + pad16(q)] = v;
+    // U(q) = W(q) + W(q + N) and V(q) = (W(q) - W(q + N)) e^{+2 pi i q/M} for
+    // the q = t + G m this thread owns in the first FFT stage, formed in
+    // registers.  W(q + N) is W(N) for q = 0 and built from the conjugates at
+    // the mirror N - q otherwise.  Each Y(q), q < N, is loaded once (all loads
+    // of the row are issued together) and its mirror is taken from the other
+    // thread through shared memory; the few band values S are loaded directly.
+    const cpx<R> z = mk<R>(R(0), R(0));
+    cpx<R> y[16], s[16], sm2[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int q = t + G * m;
+      const int qm = (q == 0) ? N : N - q;
+      y[m] = valid ? A[Tile<R>::at(row, q, ldqA)] : z;
+      s[m] = (valid && q <= Q) ? St[Tile<R>::at(row, q, ldqB)] : z;
+      sm2[m] = (valid && qm <= Q) ? St[Tile<R>::at(row, qm, ldqB)] : z;
     }
+    const cpx<R> yN = (valid && t == 0) ? A[Tile<R>::at(row, N, ldqA)] : z;
+    __syncthreads();  // the previous transform's last-stage loads of buf_u are done
+#pragma unroll
+    for (int m = 0; m < 16; ++m) buf_u[pad16(t + G * m)] = y[m];
     __syncthreads();
+    cpx<R> ym[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int q = t + G * m;
+      ym[m] = (q == 0) ? yN : buf_u[pad16(N - q)];
+    }
     cpx<R> a[16], b[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-      a[m] = buf_u[pad16(t + G * m)];
-      b[m] = buf_v[pad16(t + G * m)];
+      const int q = t + G * m;
+      cpx<R> yh = ym[m], sh = sm2[m];
+      if (q != 0) {
+        yh = conj(yh);
+        sh = conj(sh);
+      }
+      const cpx<R> wlo = y[m] + mul_i(s[m], si);
+      const cpx<R> whi = yh + mul_i(sh, si);
+      a[m] = wlo + whi;
+      const cpx<R> w = twm(ax, q);  // e^{-2 pi i q/M}; the inverse uses its conjugate
+      const cpx<R> d = wlo - whi;
+      b[m] = cj ? cmul(d, w) : cmulc(d, w);
     }
     block_fft2_regs<R, LOG2N>(a, b, buf_u, buf_v, t, stw, cj == 0);
     if (valid) {
