@@ -394,6 +394,22 @@ def run_ours(args):
     phi_64 = plan64.solve(ins[0]).cpu().numpy()
     plan64.close()
 
+    # ---- the standard periodic FFT solver (no split, no padding) on the same input
+    standard = {}
+    for prec, reps in (("mixed", max(3, min(args.steps, 200))), ("fp64", max(3, min(args.steps, 20)))):
+        ps = Plan(n, lx=L, partition="none", precision=prec, device=dev)
+        for i in range(2):
+            ps.solve(ins[i % N_ROT], outs[i % N_ROT])
+        barrier()
+        e0.record(stream)
+        for i in range(reps):
+            ps.solve(ins[i % N_ROT], outs[i % N_ROT])
+        e1.record(stream)
+        barrier()
+        ts = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
+        standard[prec] = {"solves_per_s": world * reps / ts, "ms_per_step": ts * 1000.0 / reps, "steps": reps}
+        ps.close()
+
     # ---- end to end through the public API with host buffers
     rho_h = torch.from_numpy(rho_np).pin_memory()
     phi_h = torch.empty_like(rho_h).pin_memory()
@@ -439,6 +455,8 @@ def run_ours(args):
         "fp64": {"value": value64, "unit": "solves/s", "ms_per_step": t64 * 1000.0 / k64, "steps": k64,
                  "dtype": "f64", "mixed_speedup": value / value64},
         "roofline": roofline,
+        "standard_fft": {"what": "standard periodic FFT solver (kappa = 1, p = 0), same grid and input",
+                         **standard},
         "e2e": e2e,
         "gpu_launches": args.steps * n_stages,
         "clocks": clk,

@@ -58,7 +58,13 @@ typedef enum {
 
 typedef enum {
   DSNU_PARTITION_GAUSS = 0,  /* p(k) = exp(-|k|^2/sigma^2) (Sec. 2.1) */
-  DSNU_PARTITION_SHARP = 1   /* p(k) = 1 on |k| <= P, 0 outside */
+  DSNU_PARTITION_SHARP = 1,  /* p(k) = 1 on |k| <= P, 0 outside */
+  DSNU_PARTITION_NONE = 2    /* p = 0 with pad_factor = 1: the standard periodic
+                                FFT solver the paper compares against (Sec. 2.1,
+                                Table 1): Phi = IDFT[-k_x^2/|k|^2 DFT(rho)] on
+                                the unpadded grid, value 0 at k = 0, dk = pi/l.
+                                cut_radius, sigma, n_r, n_theta, kernel_width
+                                are ignored. */
 } dsnu_partition;
 
 /* Solver parameters (Sec. 2.1).  Zero-valued optional fields take defaults. */
@@ -74,7 +80,8 @@ typedef struct {
                               n_theta even (node set symmetric under k -> -k) */
   int32_t kernel_width;    /* ES kernel width w in fine-grid cells, 2..16;
                               0 => 15 (FP64) or 8 (MIXED) */
-  int32_t pad_factor;      /* kappa; 0 or 2 (only 2 is supported) */
+  int32_t pad_factor;      /* kappa; 0 or 2 for the split solver, 1 (and only 1)
+                              with DSNU_PARTITION_NONE */
   int32_t precision;       /* dsnu_precision */
   int32_t partition;       /* dsnu_partition */
 } dsnu_params;
@@ -203,8 +210,11 @@ dsnu_status dsnu_ds_plan_create(const dsnu_ds_params* params, void* stream, dsnu
 
 /* Load the phases of the linear flow over a step tau (eqs. 1st_tssp,
  * 1st_tssp_more): e^{-i tau (k_x^2 - alpha k_y^2)}, k angular wave numbers of
- * the periodic grid.  Generated in FP64 on the host and uploaded (synchronises
- * `stream`) unless the same (tau, alpha) is already loaded. */
+ * the periodic grid.  A small kernel on `stream` evaluates them in FP64 (no
+ * host round trip, no synchronisation) unless the same (tau, alpha) is
+ * already loaded; later dsnu_ds_linear calls must use the same stream (or be
+ * ordered after it).  Errors: DSNU_EINVAL (NULL plan, non-finite values),
+ * DSNU_ECUDA (launch failed). */
 dsnu_status dsnu_ds_set_linear_step(dsnu_ds_plan plan, double tau, double alpha, void* stream);
 
 /* u <- F^-1[ e^{-i tau (k_x^2 - alpha k_y^2)} F[u] ] in place (the exact

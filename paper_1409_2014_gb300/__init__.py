@@ -12,21 +12,25 @@ from __future__ import annotations
 
 from . import _abi
 from ._abi import (  # noqa: F401
-    DSNU_FP64, DSNU_MIXED, DSNU_PARTITION_GAUSS, DSNU_PARTITION_SHARP, DsnuError,
+    DSNU_FP64, DSNU_MIXED, DSNU_PARTITION_GAUSS, DSNU_PARTITION_SHARP, DSNU_PARTITION_NONE, DsnuError,
     dsnu_last_error, dsnu_params, dsnu_plan_create, dsnu_plan_destroy, dsnu_plan_get_info,
     dsnu_set_workspace, dsnu_solve, dsnu_solve_adjoint, dsnu_status_poll, dsnu_workspace_bytes,
     dsnu_solve_host, dsnu_profile_begin, dsnu_profile_end, dsnu_stage_count, dsnu_stage_name,
 )
 
 _PREC = {"fp64": DSNU_FP64, "mixed": DSNU_MIXED}
-_PART = {"gauss": DSNU_PARTITION_GAUSS, "sharp": DSNU_PARTITION_SHARP}
+_PART = {"gauss": DSNU_PARTITION_GAUSS, "sharp": DSNU_PARTITION_SHARP, "none": DSNU_PARTITION_NONE}
 
 
 def make_params(nx, ny, lx, ly, cut_radius, n_r, n_theta, sigma=0.0, kernel_width=0,
                 precision="fp64", partition="gauss") -> dsnu_params:
+    """partition "none" selects the standard periodic FFT solver (no split, no
+    padding: pad_factor 1); the polar parameters are then ignored."""
+    standard = partition == "none"
     return dsnu_params(nx=int(nx), ny=int(ny), lx=float(lx), ly=float(ly),
-                       cut_radius=float(cut_radius), sigma=float(sigma), n_r=int(n_r),
-                       n_theta=int(n_theta), kernel_width=int(kernel_width), pad_factor=2,
+                       cut_radius=float(cut_radius or 0.0), sigma=float(sigma), n_r=int(n_r or 0),
+                       n_theta=int(n_theta or 0), kernel_width=int(kernel_width),
+                       pad_factor=1 if standard else 2,
                        precision=_PREC[precision], partition=_PART[partition])
 
 

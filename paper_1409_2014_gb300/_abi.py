@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libdsnufft.so")
 
 DSNU_OK, DSNU_EINVAL, DSNU_ENOMEM, DSNU_ECUDA, DSNU_ETIMEOUT, DSNU_EUNSUPPORTED = range(6)
 DSNU_FP64, DSNU_MIXED = 0, 1
-DSNU_PARTITION_GAUSS, DSNU_PARTITION_SHARP = 0, 1
+DSNU_PARTITION_GAUSS, DSNU_PARTITION_SHARP, DSNU_PARTITION_NONE = 0, 1, 2
 
 STATUS_NAMES = {0: "DSNU_OK", 1: "DSNU_EINVAL", 2: "DSNU_ENOMEM", 3: "DSNU_ECUDA",
                 4: "DSNU_ETIMEOUT", 5: "DSNU_EUNSUPPORTED"}

@@ -13,6 +13,8 @@ namespace dsnu {
 
 // Device tables of a plan.  Real-valued tables are in the plan's working
 // precision (float for DSNU_MIXED, double for DSNU_FP64); node_D is FP64.
+// The standard solver uses stw_x, stw_y, m_wx2 ((q_x dk_x)^2, q_x <= nx/2)
+// and status only.
 struct PlanTables {
   void* stw_x;    // cpx, FFT stage twiddles of length nx (fft_stage_tw_elems)
   void* twm_lo_x; // cpx, e^{-2 pi i n/Mx}, n < Lx = min(64, nx)
@@ -70,8 +72,9 @@ struct PlanGeom {
   int spread_cfg;          // index into kSpreadCfgs (chosen by the autotuner)
   int spread_tile;         // its tile edge (cells)
   int precision, sharp;
+  int standard;  // 1: the standard periodic FFT solver (kappa = 1, p = 0; standard.cuh)
   double beta, sigma, cut_radius;
-  double scale;  // 1/(Mx My)
+  double scale;  // 1/(Mx My) (split solver) or 1/(nx ny) (standard solver)
 };
 
 constexpr int kStages = 8;       // kernels per solve

@@ -3,6 +3,7 @@
 
 #include "internal.h"
 #include "kernels.cuh"
+#include "standard.cuh"
 
 namespace dsnu {
 
@@ -60,9 +61,45 @@ cudaError_t prepare_cols(PlanGeom& g) {
   return resident_ctas(k_band_inv<R, L2>, GG::T_C, GG::smem_col, &g.cap_bandi);
 }
 
+template <typename R, int L2>
+cudaError_t prepare_std_rows(PlanGeom& g) {
+  using GS = GeoStd<R, L2>;
+  const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_std_row_fwd<R, L2>, A, int(GS::smem)))) return e;
+  if ((e = cudaFuncSetAttribute(k_std_row_inv<R, L2>, A, int(GS::smem)))) return e;
+  if ((e = resident_ctas(k_std_row_fwd<R, L2>, GS::T, GS::smem, &g.cap_rowf))) return e;
+  return resident_ctas(k_std_row_inv<R, L2>, GS::T, GS::smem, &g.cap_rowi);
+}
+
+template <typename R, int L2>
+cudaError_t prepare_std_cols(PlanGeom& g) {
+  using GS = GeoStd<R, L2>;
+  cudaError_t e = cudaFuncSetAttribute(k_std_col<R, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(GS::smem));
+  if (e) return e;
+  return resident_ctas(k_std_col<R, L2>, GS::T, GS::smem, &g.cap_col);
+}
+
 template <typename R>
 cudaError_t prepare_kernels(PlanGeom& g) {
   cudaError_t e = cudaSuccess;
+  if (g.standard) {
+#define DSNU_PREP_SR(L2) e = prepare_std_rows<R, L2>(g)
+#define DSNU_PREP_SC(L2) e = prepare_std_cols<R, L2>(g)
+    switch (g.log2nx) {
+      DSNU_LOG2_CASES(DSNU_PREP_SR)
+      default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    switch (g.log2ny) {
+      DSNU_LOG2_CASES(DSNU_PREP_SC)
+      default: return cudaErrorInvalidValue;
+    }
+#undef DSNU_PREP_SR
+#undef DSNU_PREP_SC
+    return e;
+  }
 #define DSNU_PREP_R(L2) e = prepare_rows<R, L2>(g)
 #define DSNU_PREP_C(L2) e = prepare_cols<R, L2>(g)
   switch (g.log2nx) {
@@ -83,9 +120,63 @@ cudaError_t prepare_kernels(PlanGeom& g) {
 // (band_fwd, interp, spread, spread_reduce, band_inv), col_main, row_inv.  With `ev`
 // (profiling) kProfEvents events are recorded before the first kernel and
 // after each kernel, in launch order.
+// The standard periodic FFT solver (standard.cuh): row_fwd, col, row_inv.
+// With `ev` the same kProfEvents events are recorded as for the split solver,
+// the band-chain stages being empty, so that the stage names keep their
+// meaning (row_fwd, col_main, row_inv).
+template <typename R>
+dsnu_status run_standard(const PlanGeom& g, const PlanTables& t, const WsLayout& L, const Members& mem,
+                         cudaStream_t st, int cj, cudaEvent_t* ev) {
+  const cpx<R>* sx = static_cast<const cpx<R>*>(t.stw_x);
+  const cpx<R>* sy = static_cast<const cpx<R>*>(t.stw_y);
+  const R* wx2 = static_cast<const R*>(t.m_wx2);
+  const long nm = mem.count;
+  const int ldq = L.ldqA;
+#define DSNU_SROWF(L2)                                                                         \
+  k_std_row_fwd<R, L2><<<persistent_grid(nm * ((g.ny / 2 + GeoStd<R, L2>::PER - 1) /            \
+                                               GeoStd<R, L2>::PER), g.cap_rowf),               \
+                         GeoStd<R, L2>::T, GeoStd<R, L2>::smem, st>>>(mem, L.off_A, ldq, g.ny, sx, cj)
+#define DSNU_SCOL(L2)                                                                          \
+  k_std_col<R, L2><<<persistent_grid(nm * ((ldq + GeoStd<R, L2>::PER - 1) / GeoStd<R, L2>::PER), \
+                                     g.cap_col),                                                \
+                     GeoStd<R, L2>::T, GeoStd<R, L2>::smem, st>>>(mem, L.off_A, ldq, ldq, sy, wx2, \
+                                                                  R(g.dky2), R(g.scale), cj)
+#define DSNU_SROWI(L2)                                                                         \
+  k_std_row_inv<R, L2><<<persistent_grid(nm * ((g.ny / 2 + GeoStd<R, L2>::PER - 1) /            \
+                                               GeoStd<R, L2>::PER), g.cap_rowi),               \
+                         GeoStd<R, L2>::T, GeoStd<R, L2>::smem, st>>>(mem, L.off_A, ldq, g.ny, sx, cj)
+  if (ev) cudaEventRecord(ev[0], st);
+  switch (g.log2nx) {
+    DSNU_LOG2_CASES(DSNU_SROWF)
+    default: return DSNU_EUNSUPPORTED;
+  }
+  if (ev)
+    for (int i = 1; i <= 6; ++i) cudaEventRecord(ev[i], st);
+  switch (g.log2ny) {
+    DSNU_LOG2_CASES(DSNU_SCOL)
+    default: return DSNU_EUNSUPPORTED;
+  }
+  if (ev) cudaEventRecord(ev[7], st);
+  switch (g.log2nx) {
+    DSNU_LOG2_CASES(DSNU_SROWI)
+    default: return DSNU_EUNSUPPORTED;
+  }
+  if (ev) cudaEventRecord(ev[8], st);
+#undef DSNU_SROWF
+#undef DSNU_SCOL
+#undef DSNU_SROWI
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("kernel launch failed: ") + cudaGetErrorString(e));
+    return DSNU_ECUDA;
+  }
+  return DSNU_OK;
+}
+
 template <typename R>
 dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout& L, const Members& mem,
                          cudaStream_t st, int cj, cudaEvent_t* ev) {
+  if (g.standard) return run_standard<R>(g, t, L, mem, st, cj, ev);
   const WsOff off{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial};
   const AxisTabs<R> ax{static_cast<const cpx<R>*>(t.stw_x), static_cast<const cpx<R>*>(t.twm_lo_x),
                        static_cast<const cpx<R>*>(t.twm_hi_x), g.log2lo_x, static_cast<const R*>(t.decon_x)};

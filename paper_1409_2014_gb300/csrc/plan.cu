@@ -473,10 +473,55 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   return setup_spread<R>(P, T.node_q0, T.node_w, st);
 }
 
+// Tables of the standard periodic FFT solver: the stage twiddles of both
+// axes and (q_x dk_x)^2 for q_x in [0, nx/2], dk = 2 pi/(2 l) (no padding).
+template <typename R>
+static dsnu_status build_tables_standard(dsnu_plan_s* P, cudaStream_t st) {
+  const dsnu_params& p = P->prm;
+  PlanGeom& g = P->geom;
+  std::vector<double> tmp;
+  fft_stage_twiddles(g.log2nx, tmp);
+  const std::vector<R> stw_x = cast<R>(tmp);
+  fft_stage_twiddles(g.log2ny, tmp);
+  const std::vector<R> stw_y = cast<R>(tmp);
+  const double dkx = M_PI / p.lx, dky = M_PI / p.ly;
+  std::vector<R> wx2(g.nx / 2 + 1);
+  for (int q = 0; q <= g.nx / 2; ++q) wx2[q] = R((q * dkx) * (q * dkx));
+  g.dky2 = dky * dky;
+  Builder b;
+  const size_t o_stx = b.add(stw_x), o_sty = b.add(stw_y), o_wx2 = b.add(wx2);
+  const int zero = 0;
+  const size_t o_st = b.add(&zero, sizeof(int));
+  void* dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, b.bytes.size());
+  if (e != cudaSuccess) return fail(DSNU_ENOMEM, std::string("cudaMalloc(plan tables): ") + cudaGetErrorString(e));
+  e = cudaMemcpyAsync(dev, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    return fail(DSNU_ECUDA, std::string("plan table upload: ") + cudaGetErrorString(e));
+  }
+  char* d = static_cast<char*>(dev);
+  PlanTables& t = P->tab;
+  t.stw_x = d + o_stx;
+  t.stw_y = d + o_sty;
+  t.m_wx2 = d + o_wx2;
+  t.status = reinterpret_cast<int*>(d + o_st);
+  P->table_block = dev;
+  P->table_bytes = b.bytes.size();
+  return DSNU_OK;
+}
+
 static void layout_workspace(dsnu_plan_s* P) {  // defined after the autotuner, which uses it
   const PlanGeom& g = P->geom;
   const size_t csz = (g.precision == DSNU_MIXED) ? 8 : 16;
   WsLayout& L = P->ws_layout;
+  if (g.standard) {  // one row-tiled half spectrum, q_x in [0, nx/2]
+    L = WsLayout{};
+    L.ldqA = g.nx / 2 + 1;
+    L.total = (size_t(g.ny) * L.ldqA * csz + 255) & ~size_t(255);
+    return;
+  }
   L.ldqA = g.nx + 1;
   L.ldqB = g.Q + 1;
   L.ldq = 2 * g.Q + 1;
@@ -510,19 +555,32 @@ dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan*
     return fail(DSNU_EINVAL, "nx, ny must be powers of two in [16, 4096]");
   if (!(p.lx > 0.0) || !(p.ly > 0.0) || !std::isfinite(p.lx) || !std::isfinite(p.ly))
     return fail(DSNU_EINVAL, "lx, ly must be positive and finite");
-  if (!(p.cut_radius > 0.0) || !std::isfinite(p.cut_radius)) return fail(DSNU_EINVAL, "cut_radius must be positive");
-  if (p.sigma < 0.0 || !std::isfinite(p.sigma)) return fail(DSNU_EINVAL, "sigma must be >= 0");
-  if (p.n_r < 1 || p.n_r > 4096) return fail(DSNU_EINVAL, "n_r must be in [1, 4096]");
-  if (p.n_theta < 2 || (p.n_theta & 1) || p.n_theta > 65536) return fail(DSNU_EINVAL, "n_theta must be even, >= 2");
   if (p.precision != DSNU_FP64 && p.precision != DSNU_MIXED) return fail(DSNU_EINVAL, "unknown precision");
-  if (p.partition != DSNU_PARTITION_GAUSS && p.partition != DSNU_PARTITION_SHARP)
+  if (p.partition != DSNU_PARTITION_GAUSS && p.partition != DSNU_PARTITION_SHARP &&
+      p.partition != DSNU_PARTITION_NONE)
     return fail(DSNU_EINVAL, "unknown partition");
-  if (p.pad_factor != 0 && p.pad_factor != 2) return fail(DSNU_EUNSUPPORTED, "only pad_factor = 2 is supported");
-  if (p.kernel_width == 0) p.kernel_width = (p.precision == DSNU_FP64) ? 15 : 8;
-  if (p.kernel_width < 2 || p.kernel_width > 16) return fail(DSNU_EINVAL, "kernel_width must be in [2, 16]");
-  if (p.sigma == 0.0) p.sigma = p.cut_radius / 6.0;
-  p.pad_factor = 2;
-  if (long(p.n_r) * long(p.n_theta) > (1L << 24)) return fail(DSNU_EINVAL, "too many polar nodes");
+  const bool standard = (p.partition == DSNU_PARTITION_NONE);
+  if (standard) {
+    // the standard periodic FFT solver: no polar part, no padding
+    if (p.pad_factor != 1) return fail(DSNU_EINVAL, "partition NONE (standard FFT solver) needs pad_factor = 1");
+    p.cut_radius = 0.0;
+    p.sigma = 0.0;
+    p.n_r = p.n_theta = p.kernel_width = 0;
+  } else {
+    if (p.pad_factor == 1) return fail(DSNU_EINVAL, "pad_factor = 1 is the standard solver: partition NONE");
+    if (p.pad_factor != 0 && p.pad_factor != 2) return fail(DSNU_EUNSUPPORTED, "only pad_factor = 2 is supported");
+    if (!(p.cut_radius > 0.0) || !std::isfinite(p.cut_radius))
+      return fail(DSNU_EINVAL, "cut_radius must be positive");
+    if (p.sigma < 0.0 || !std::isfinite(p.sigma)) return fail(DSNU_EINVAL, "sigma must be >= 0");
+    if (p.n_r < 1 || p.n_r > 4096) return fail(DSNU_EINVAL, "n_r must be in [1, 4096]");
+    if (p.n_theta < 2 || (p.n_theta & 1) || p.n_theta > 65536)
+      return fail(DSNU_EINVAL, "n_theta must be even, >= 2");
+    if (p.kernel_width == 0) p.kernel_width = (p.precision == DSNU_FP64) ? 15 : 8;
+    if (p.kernel_width < 2 || p.kernel_width > 16) return fail(DSNU_EINVAL, "kernel_width must be in [2, 16]");
+    if (p.sigma == 0.0) p.sigma = p.cut_radius / 6.0;
+    p.pad_factor = 2;
+    if (long(p.n_r) * long(p.n_theta) > (1L << 24)) return fail(DSNU_EINVAL, "too many polar nodes");
+  }
 
   dsnu_plan_s* P = new (std::nothrow) dsnu_plan_s();
   if (!P) return fail(DSNU_ENOMEM, "host allocation failed");
@@ -530,8 +588,9 @@ dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan*
   PlanGeom& g = P->geom;
   g.nx = p.nx;
   g.ny = p.ny;
-  g.mx = 2 * p.nx;
-  g.my = 2 * p.ny;
+  g.standard = standard ? 1 : 0;
+  g.mx = p.pad_factor * p.nx;
+  g.my = p.pad_factor * p.ny;
   g.log2nx = ilog2(p.nx);
   g.log2ny = ilog2(p.ny);
   g.w = p.kernel_width;
@@ -543,7 +602,11 @@ dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan*
   g.sharp = (p.partition == DSNU_PARTITION_SHARP);
   g.scale = 1.0 / (double(g.mx) * double(g.my));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  dsnu_status s = (p.precision == DSNU_MIXED) ? build_tables<float>(P, st) : build_tables<double>(P, st);
+  dsnu_status s;
+  if (standard)
+    s = (p.precision == DSNU_MIXED) ? build_tables_standard<float>(P, st) : build_tables_standard<double>(P, st);
+  else
+    s = (p.precision == DSNU_MIXED) ? build_tables<float>(P, st) : build_tables<double>(P, st);
   if (s != DSNU_OK) {
     if (P->spread_block) cudaFree(P->spread_block);
     if (P->table_block) cudaFree(P->table_block);

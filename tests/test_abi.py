@@ -71,6 +71,20 @@ def test_unsupported_padding(lib):
     assert ei.value.status == _abi.DSNU_EUNSUPPORTED
 
 
+def test_standard_solver_needs_pad_factor_one(lib):
+    """partition NONE is the unpadded standard solver: pad_factor must be 1,
+    and pad_factor 1 is accepted only with partition NONE."""
+    p = _params(partition="none")
+    assert p.pad_factor == 1 and p.partition == _abi.DSNU_PARTITION_NONE
+    for part, pad in ((_abi.DSNU_PARTITION_NONE, 2), (_abi.DSNU_PARTITION_NONE, 0),
+                      (_abi.DSNU_PARTITION_GAUSS, 1), (_abi.DSNU_PARTITION_SHARP, 1), (3, 1)):
+        q = _params()
+        q.partition, q.pad_factor = part, pad
+        with pytest.raises(_abi.DsnuError) as ei:
+            _abi.dsnu_plan_create(q, 0)
+        assert ei.value.status == _abi.DSNU_EINVAL
+
+
 def test_null_plan_calls(lib):
     assert lib.dsnu_workspace_bytes(None) == 0
     assert lib.dsnu_solve(None, None, None, None) == _abi.DSNU_EINVAL
