@@ -57,3 +57,47 @@ def test_table8_moving_lump(L, h, printed):
     ex = D.arkadiev_lump(X, Y, T)
     err = float(np.linalg.norm(u - ex) / np.linalg.norm(ex))
     assert abs(err / printed - 1.0) < 0.01, err
+
+
+# ---------------------------------------------------------------- Yoshida (Sec. 2.3)
+
+def test_yoshida_coefficients_satisfy_the_order_conditions():
+    """Consistency (sum a = sum b = 1), symmetry, and the third-order condition
+    of the triple jump, b1^3 + b2^3 + b3^3 = 0, that makes the symmetric
+    composition fourth order."""
+    a, b = D.yoshida_coefficients()
+    assert abs(sum(a) - 1.0) < 1e-15 and abs(sum(b) - 1.0) < 1e-15
+    assert a[0] == a[3] and a[1] == a[2] and b[0] == b[2]
+    assert abs(sum(x ** 3 for x in b)) < 1e-14
+    assert b[1] < 0 and a[1] < 0  # the backward sub-steps of the triple jump
+
+
+def _order_case():
+    n, L = 32, 8.0
+    p = OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=4.0, sigma=2 / 3, n_r=16, n_theta=32)
+    return p, synth.wavefunction_sum(n, n, L, L, seed=4, count=3)
+
+
+def _evolve(step, u, p, tau, T, alpha=1.0, beta=1.0):
+    for _ in range(int(round(abs(T / tau)))):
+        u = step(u, p, tau, alpha, beta)
+    return u
+
+
+def test_yoshida_is_fourth_order_and_strang_second_order():
+    """Global error at T = 0.16 against a Yoshida run with tau = 0.0025: halving
+    tau divides the Yoshida error by ~16 and the Strang error by ~4."""
+    p, u0 = _order_case()
+    ref = _evolve(D.yoshida_step, u0, p, 0.0025, 0.16)
+    for step, lo, hi in ((D.yoshida_step, 13.0, 19.0), (D.strang_step, 3.5, 4.5)):
+        e = [np.abs(_evolve(step, u0, p, tau, 0.16) - ref).max() for tau in (0.04, 0.02, 0.01)]
+        for k in range(2):
+            assert lo < e[k] / e[k + 1] < hi, (step.__name__, e)
+
+
+def test_yoshida_conserves_mass_and_is_reversible():
+    p, u0 = _order_case()
+    u = _evolve(D.yoshida_step, u0, p, 0.02, 0.1)
+    assert abs(np.sum(np.abs(u) ** 2) / np.sum(np.abs(u0) ** 2) - 1.0) < 1e-13
+    u = _evolve(D.yoshida_step, u, p, -0.02, 0.1)
+    assert np.abs(u - u0).max() < 1e-12 * np.abs(u0).max()
