@@ -24,6 +24,7 @@ from .potential import (  # noqa: F401
     OracleParams,
     grid_axis,
     polar_nodes,
+    radial_rule,
     polar_weights,
     partition,
     multiplier_high,

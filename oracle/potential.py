@@ -23,8 +23,9 @@ Conventions (each one is a reading of the paper; all are pinned by tests):
   m1 = (1 - p) m with m1(0) = 0, inverse FFT, restriction to the physical
   N x N points.
 * I2 (eq. I2PolarDisc): radial Gauss-Legendre nodes on [0, P] (the Jacobian r
-  folded into the weight) times the uniform angular rule theta_j = 2 pi j /
-  N_theta; weights D = -(2 pi)^-2 r w_r (2 pi / N_theta) cos^2(theta) p(r).
+  folded into the weight), or the Gauss-Jacobi rule whose weight function is
+  that Jacobian (Sec. 2.1), times the uniform angular rule theta_j = 2 pi j /
+  N_theta; weights D = -(2 pi)^-2 W_r (2 pi / N_theta) cos^2(theta) p(r).
   rho_hat at the nodes is the trapezoid sum h_x h_y sum_n rho_n e^{-i k.x_n}
   (the exact sum that a type-2 NUFFT approximates, eq. 2.2); I2 is
   Re sum_j D_j rho_hat_j e^{+i k_j.x_n} (the exact sum a type-1 NUFFT
@@ -39,6 +40,7 @@ import dataclasses
 import math
 
 import numpy as np
+import scipy.special
 import scipy.fft as sfft
 
 TWO_PI = 2.0 * math.pi
@@ -59,6 +61,7 @@ class OracleParams:
     sigma: float = 0.0
     pad: int = 2
     partition: str = "gauss"
+    radial: str = "legendre"  # "legendre" (Jacobian r in the weight) or "jacobi" (weight (1+t), Sec. 2.1)
 
     @property
     def hx(self) -> float:
@@ -141,30 +144,45 @@ def i1_padded_fft_adjoint(g: np.ndarray, p: OracleParams) -> np.ndarray:
     return np.ascontiguousarray(out[:ny, :nx].real)
 
 
+def radial_rule(p: OracleParams):
+    """Nodes r_i in (0, P) and weights W_i with sum_i W_i f(r_i) ~ int_0^P f(r) r dr.
+
+    "legendre": Gauss-Legendre on [0, P] (numpy's table mapped affinely) with
+    the Jacobian r multiplied into the weight.  "jacobi": the Gauss-Jacobi rule
+    the paper names (Sec. 2.1) for the weight (1 - t)^0 (1 + t)^1 on [-1, 1]
+    (scipy's table), which is the Jacobian itself: with r = P (1 + t)/2,
+    r dr = (P/2)^2 (1 + t) dt."""
+    if p.radial == "legendre":
+        t, v = np.polynomial.legendre.leggauss(p.n_r)
+        r = 0.5 * p.cut_radius * (t + 1.0)
+        return r, r * (0.5 * p.cut_radius * v)
+    if p.radial == "jacobi":
+        t, v = scipy.special.roots_jacobi(p.n_r, 0.0, 1.0)
+        return 0.5 * p.cut_radius * (t + 1.0), (0.5 * p.cut_radius) ** 2 * v
+    raise ValueError(f"unknown radial rule {p.radial!r}")
+
+
 def polar_nodes(p: OracleParams):
     """Polar quadrature nodes of eq. I2PolarDisc.
 
-    Radial: Gauss-Legendre on [0, P] (numpy's table mapped affinely), the
-    Jacobian r is applied in ``polar_weights``.  Angular: theta_j = 2 pi j /
-    N_theta with weight 2 pi / N_theta (trapezoid rule on the circle).
+    Radial: ``radial_rule`` (weights for int f(r) r dr).  Angular: theta_j =
+    2 pi j / N_theta with weight 2 pi / N_theta (trapezoid rule on the circle).
     Node order: radial index major, angular index minor.
-    Returns (kx, ky, r, w_r, theta)."""
-    t, v = np.polynomial.legendre.leggauss(p.n_r)
-    r = 0.5 * p.cut_radius * (t + 1.0)
-    w_r = 0.5 * p.cut_radius * v
+    Returns (kx, ky, r, W_r, theta)."""
+    r, w_rad = radial_rule(p)
     theta = TWO_PI * np.arange(p.n_theta, dtype=np.float64) / p.n_theta
     kx = (r[:, None] * np.cos(theta)[None, :]).ravel()
     ky = (r[:, None] * np.sin(theta)[None, :]).ravel()
-    return kx, ky, r, w_r, theta
+    return kx, ky, r, w_rad, theta
 
 
 def polar_weights(p: OracleParams) -> np.ndarray:
-    """D_j = -(2 pi)^-2 r w_r (2 pi/N_theta) cos^2(theta) p(r): the weights of
-    eq. I2PolarDisc with the Jacobian r and the (2 pi)^-2 of the angular
-    frequency convention written in."""
-    _, _, r, w_r, theta = polar_nodes(p)
+    """D_j = -(2 pi)^-2 W_r (2 pi/N_theta) cos^2(theta) p(r): the weights of
+    eq. I2PolarDisc with the Jacobian r (inside W_r) and the (2 pi)^-2 of the
+    angular frequency convention written in."""
+    _, _, r, w_rad, theta = polar_nodes(p)
     w_theta = TWO_PI / p.n_theta
-    radial = r * w_r * partition(r * r, p)
+    radial = w_rad * partition(r * r, p)
     ang = np.cos(theta) ** 2 * w_theta
     return (-(radial[:, None] * ang[None, :]) / TWO_PI**2).ravel()
 

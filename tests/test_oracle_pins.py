@@ -42,11 +42,13 @@ def _matches_printed(value, printed, rel):
 
 # ---------------------------------------------------------------- closed forms
 
-def test_gaussian_closed_form_resolved():
+@pytest.mark.parametrize("rule", ["legendre", "jacobi"])
+def test_gaussian_closed_form_resolved(rule):
     """rho = exp(-r^2) on [-16,16)^2, N = 128, P = 4, sigma = 2/3 with a
-    resolved polar rule: Phi matches the closed form to rounding."""
+    resolved polar rule (either radial rule): Phi matches the closed form to
+    rounding."""
     p = OracleParams(nx=128, ny=128, lx=16, ly=16, cut_radius=4.0, sigma=2 / 3,
-                     n_r=48, n_theta=96)
+                     n_r=48, n_theta=96, radial=rule)
     X, Y = _grid(128, 16)
     phi, i1, i2 = O.solve(np.exp(-(X**2 + Y**2)), p, return_parts=True)
     ex = O.gaussian_potential(X, Y)
@@ -146,16 +148,22 @@ def test_table5_split_solver_arkadiev(L, h, printed):
 
 # ---------------------------------------------------------------- quadrature
 
+@pytest.mark.parametrize("rule,extra", [("legendre", 0), ("jacobi", 1)])
 @pytest.mark.parametrize("n_r", [1, 7, 32, 64])
-def test_radial_rule_exact_for_polynomials(n_r):
-    """Gauss-Legendre on [0, P] integrates r^k exactly for k <= 2 n_r - 1."""
+def test_radial_rule_exact_for_polynomials(n_r, rule, extra):
+    """The radial weights W integrate f(r) r dr on [0, P]: exactly for
+    f = r^k with k <= 2 n_r - 2 (Gauss-Legendre times r) and k <= 2 n_r - 1
+    (Gauss-Jacobi, whose weight function is r itself)."""
     P = 3.7
-    p = OracleParams(nx=8, ny=8, lx=1, ly=1, cut_radius=P, n_r=n_r, n_theta=4)
-    _, _, r, w_r, _ = O.polar_nodes(p)
-    for k in range(0, 2 * n_r):
-        exact = P ** (k + 1) / (k + 1)
-        assert abs(np.sum(w_r * r**k) / exact - 1.0) < 1e-13
-    assert np.all((r > 0) & (r < P))
+    p = OracleParams(nx=8, ny=8, lx=1, ly=1, cut_radius=P, n_r=n_r, n_theta=4, radial=rule)
+    r, w = O.radial_rule(p)
+    for k in range(0, 2 * n_r - 1 + extra):
+        exact = P ** (k + 2) / (k + 2)
+        assert abs(np.sum(w * r**k) / exact - 1.0) < 1e-13, k
+    assert np.all((r > 0) & (r < P)) and np.all(np.diff(r) > 0)
+    if n_r <= 7:  # one degree more is not integrated exactly (not over-specified)
+        k = 2 * n_r - 1 + extra
+        assert abs(np.sum(w * r**k) / (P ** (k + 2) / (k + 2)) - 1.0) > 1e-8
 
 
 def test_angular_rule_and_weights():
