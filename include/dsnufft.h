@@ -67,6 +67,12 @@ typedef enum {
                                 are ignored. */
 } dsnu_partition;
 
+typedef enum {
+  DSNU_RADIAL_LEGENDRE = 0,  /* Gauss-Legendre on [0, P], the Jacobian r in the weights */
+  DSNU_RADIAL_JACOBI = 1     /* Gauss-Jacobi for the weight (1 + t) on [-1, 1], i.e.
+                                the Jacobian r itself (Sec. 2.1) */
+} dsnu_radial_rule;
+
 /* Solver parameters (Sec. 2.1).  Zero-valued optional fields take defaults. */
 typedef struct {
   int32_t nx, ny;          /* grid points per axis: powers of two, 16..4096 */
@@ -84,6 +90,8 @@ typedef struct {
                               with DSNU_PARTITION_NONE */
   int32_t precision;       /* dsnu_precision */
   int32_t partition;       /* dsnu_partition */
+  int32_t radial_rule;     /* dsnu_radial_rule of the polar quadrature */
+  int32_t reserved;        /* set to 0 */
 } dsnu_params;
 
 typedef struct dsnu_plan_s* dsnu_plan;
@@ -162,6 +170,29 @@ dsnu_status dsnu_profile_begin(dsnu_plan plan, int max_solves);
 dsnu_status dsnu_profile_end(dsnu_plan plan, double* stage_ms, int n_stages, int* n_solves);
 
 /* Number of kernels one solve launches, and their names (static strings). */
+/* The radial rule of the polar quadrature (eq. I2PolarDisc), host only, no
+ * device needed: n_r nodes r[i] in (0, cut_radius), ascending, and weights
+ * w[i] with sum_i w[i] f(r[i]) ~ int_0^P f(r) r dr (the polar Jacobian
+ * included), exact for f a polynomial of degree 2 n_r - 2 (Legendre) or
+ * 2 n_r - 1 (Jacobi).  r and w: caller-owned host arrays of n_r doubles.
+ * Errors: DSNU_EINVAL (n_r outside [1, 4096], cut_radius <= 0, NULL arrays,
+ * unknown rule). */
+dsnu_status dsnu_radial_nodes(int32_t n_r, int32_t rule, double cut_radius, double* r, double* w);
+
+/* Parameters for a target accuracy eps of the split solver (host only): the
+ * partition width sigma = 12 / min(lx, ly) (sigma = O(1/L), Sec. 2.1: the
+ * padded uniform grid resolves the transition of 1 - p), the disk radius
+ * P = sigma sqrt(ln(1/eps)) (p(P) = eps), and polar node counts that grow
+ * with the largest phase P R of e^{i k.x} on the disk, R = sqrt(lx^2 + ly^2):
+ * n_theta = the multiple of 4 >= P R + 16, n_r = the multiple of 8 >= P R/2 + 4
+ * (measured on the closed-form Gaussian of Sec. 3 for eps = 1e-6..1e-14),
+ * with the Gauss-Jacobi radial rule and the default ES width.  eps is clamped
+ * to [1e-15, 1e-2] (FP64) or [1e-7, 1e-2] (MIXED).
+ * Errors: DSNU_EINVAL (bad sizes or eps; or the grid is too coarse for the
+ * disk plus the ES stencil), *out untouched. */
+dsnu_status dsnu_params_auto(int32_t nx, int32_t ny, double lx, double ly, double eps, int32_t precision,
+                             dsnu_params* out);
+
 int32_t dsnu_stage_count(void);
 const char* dsnu_stage_name(int32_t stage);
 

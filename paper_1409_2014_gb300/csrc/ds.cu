@@ -173,6 +173,29 @@ __global__ void k_nonlinear_vjp_finish(const cpx<R>* __restrict__ u, const doubl
   }
 }
 
+// Linear-flow phase tables in FFT order: px[q] = e^{-i tau k_x^2} and
+// py[q] = e^{+i tau alpha k_y^2}, k = qs dk with qs the signed index.  The
+// angles and their sine/cosine are formed in FP64 and rounded to the plan's
+// precision; launched on the caller's stream, so a change of step size needs
+// no host round trip.
+template <typename R>
+__global__ void k_phase_tables(cpx<R>* __restrict__ px, cpx<R>* __restrict__ py, int nx, int ny, double dkx,
+                               double dky, double tau, double alpha) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nx) {
+    const double k = double(i < nx / 2 ? i : i - nx) * dkx;
+    double s, c;
+    sincos(-tau * k * k, &s, &c);
+    px[i] = mk<R>(R(c), R(s));
+  }
+  if (i < ny) {
+    const double k = double(i < ny / 2 ? i : i - ny) * dky;
+    double s, c;
+    sincos(tau * alpha * k * k, &s, &c);
+    py[i] = mk<R>(R(c), R(s));
+  }
+}
+
 }  // namespace dsnu
 
 using namespace dsnu;
@@ -381,32 +404,19 @@ dsnu_status dsnu_ds_set_linear_step(dsnu_ds_plan plan, double tau, double alpha,
   if (!std::isfinite(tau) || !std::isfinite(alpha)) return ds_fail(DSNU_EINVAL, "tau, alpha must be finite");
   if (plan->has_phase && plan->tau == tau && plan->alpha == alpha) return DSNU_OK;
   const dsnu_ds_params& p = plan->prm;
-  const double hx = 2.0 * p.lx / p.nx, hy = 2.0 * p.ly / p.ny;
-  std::vector<double> px(2 * size_t(p.nx)), py(2 * size_t(p.ny));
-  for (int q = 0; q < p.nx; ++q) {
-    const int qs = q < p.nx / 2 ? q : q - p.nx;
-    const double k = 2.0 * M_PI * qs / (p.nx * hx);
-    const double a = -tau * k * k;
-    px[2 * q] = std::cos(a);
-    px[2 * q + 1] = std::sin(a);
-  }
-  for (int q = 0; q < p.ny; ++q) {
-    const int qs = q < p.ny / 2 ? q : q - p.ny;
-    const double k = 2.0 * M_PI * qs / (p.ny * hy);
-    const double a = tau * alpha * k * k;
-    py[2 * q] = std::cos(a);
-    py[2 * q + 1] = std::sin(a);
-  }
-  cudaError_t e = cudaSuccess;
+  const double dkx = M_PI / p.lx, dky = M_PI / p.ly;  // 2 pi / (n h), h = 2 l / n
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (p.precision == DSNU_MIXED) {
-    upload<float>(plan->px, px, st, &e);
-    upload<float>(plan->py, py, st, &e);
-  } else {
-    upload<double>(plan->px, px, st, &e);
-    upload<double>(plan->py, py, st, &e);
-  }
-  if (e != cudaSuccess) return ds_fail(DSNU_ECUDA, std::string("phase upload: ") + cudaGetErrorString(e));
+  const int n = p.nx > p.ny ? p.nx : p.ny;
+  if (p.precision == DSNU_MIXED)
+    k_phase_tables<float><<<(n + 255) / 256, 256, 0, st>>>(static_cast<cpx<float>*>(plan->px),
+                                                           static_cast<cpx<float>*>(plan->py), p.nx, p.ny,
+                                                           dkx, dky, tau, alpha);
+  else
+    k_phase_tables<double><<<(n + 255) / 256, 256, 0, st>>>(static_cast<cpx<double>*>(plan->px),
+                                                            static_cast<cpx<double>*>(plan->py), p.nx, p.ny,
+                                                            dkx, dky, tau, alpha);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return ds_fail(DSNU_ECUDA, std::string("phase tables: ") + cudaGetErrorString(e));
   plan->tau = tau;
   plan->alpha = alpha;
   plan->has_phase = true;

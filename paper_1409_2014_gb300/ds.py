@@ -6,8 +6,11 @@
   method (Sec. 2.3 of the paper, in its symmetric form): half a linear flow,
   a full nonlinear flow with Phi = A |u|^2 frozen, half a linear flow.  Both
   flows and their vector-Jacobian products run in the library's kernels.
-* ``evolve(u0, steps, ...)``: many Strang steps, optionally with checkpointed
-  recomputation (torch.utils.checkpoint) every ``checkpoint_every`` steps.
+* ``yoshida_step(u, ...)``: one step of the fourth-order composition the paper
+  integrates with (Sec. 2.3): four linear and three nonlinear sub-flows.
+* ``evolve(u0, steps, ...)``: many steps of either scheme, optionally with
+  checkpointed recomputation (torch.utils.checkpoint) every
+  ``checkpoint_every`` steps.
 
 Gradients follow PyTorch's convention for complex inputs of a real loss:
 dL/dRe + i dL/dIm.
@@ -163,14 +166,37 @@ def strang_step(u, ds: DSPlan, solver: Plan, tau, alpha, beta):
     return LinearFlow.apply(u, ds, 0.5 * tau, alpha)
 
 
-def evolve(u0, steps, ds: DSPlan, solver: Plan, tau, alpha, beta, checkpoint_every=0):
-    """``steps`` Strang steps; with checkpoint_every > 0 only the input of every
-    segment of that many steps is kept for the backward pass, and each segment
-    is recomputed during backward."""
+_CBRT2 = 2.0 ** (1.0 / 3.0)
+# Sec. 2.3: b1 = b3 = 1/(2 - 2^(1/3)), b2 = -2^(1/3) b3, a1 = a4 = b3/2,
+# a2 = a3 = (b3 + b2)/2
+YOSHIDA_B = (1.0 / (2.0 - _CBRT2), -_CBRT2 / (2.0 - _CBRT2), 1.0 / (2.0 - _CBRT2))
+YOSHIDA_A = (0.5 * YOSHIDA_B[0], 0.5 * (YOSHIDA_B[0] + YOSHIDA_B[1]),
+             0.5 * (YOSHIDA_B[0] + YOSHIDA_B[1]), 0.5 * YOSHIDA_B[0])
+
+
+def yoshida_step(u, ds: DSPlan, solver: Plan, tau, alpha, beta):
+    """u <- A(a1 tau) B(b1 tau) A(a2 tau) B(b2 tau) A(a3 tau) B(b3 tau) A(a4 tau) u
+    (Sec. 2.3; the rightmost sub-flow acts first).  Each nonlinear sub-flow
+    freezes Phi of the field it starts from."""
+    u = LinearFlow.apply(u, ds, YOSHIDA_A[3] * tau, alpha)
+    for j in (2, 1, 0):
+        u = NonlinearFlow.apply(u, ds, solver, YOSHIDA_B[j] * tau, beta)
+        u = LinearFlow.apply(u, ds, YOSHIDA_A[j] * tau, alpha)
+    return u
+
+
+_SCHEMES = {"strang": strang_step, "yoshida": yoshida_step}
+
+
+def evolve(u0, steps, ds: DSPlan, solver: Plan, tau, alpha, beta, checkpoint_every=0, scheme="strang"):
+    """``steps`` steps of ``scheme`` ("strang" or "yoshida"); with
+    checkpoint_every > 0 only the input of every segment of that many steps is
+    kept for the backward pass, and each segment is recomputed during backward."""
+    step = _SCHEMES[scheme]
 
     def segment(u, n):
         for _ in range(n):
-            u = strang_step(u, ds, solver, tau, alpha, beta)
+            u = step(u, ds, solver, tau, alpha, beta)
         return u
 
     u = u0

@@ -10,6 +10,7 @@ import oracle
 from oracle import OracleParams
 from oracle import ds as D
 import synth
+from conftest import read_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -190,3 +191,101 @@ def test_ds_loop_complex64_gradient_vs_complex128():
         ds.close()
     ref = grads["fp64"]
     assert np.abs(grads["mixed"] - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- Yoshida (Sec. 2.3)
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_yoshida_steps_match_oracle(prec):
+    from paper_1409_2014_gb300.ds import evolve
+
+    n, L, tau = 64, 8.0, 0.01
+    solver, ds = _plans(n, L, prec)
+    p = OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=4.0, sigma=2 / 3, n_r=24, n_theta=48)
+    u_np = synth.wavefunction_sum(n, n, L, L, seed=4, count=3)
+    ref = u_np.copy()
+    for _ in range(3):
+        ref = D.yoshida_step(ref, p, tau, 1.0, -1.0)
+    with torch.no_grad():
+        out = evolve(torch.from_numpy(u_np).to(CDT[prec]).cuda(), 3, ds, solver, tau, 1.0, -1.0,
+                     scheme="yoshida")
+    out = out.cpu().numpy()
+    assert np.abs(out - ref).max() <= 10 * TOL[prec] * np.abs(ref).max()
+    solver.close()
+    ds.close()
+
+
+def test_yoshida_gradient_checkpointed_equals_full_tape_and_fd():
+    from paper_1409_2014_gb300.ds import evolve
+
+    n, L, tau, steps = 256, 16.0, 2e-3, 12
+    solver, ds = _plans(n, L, "fp64", P=6.0, n_r=32, n_theta=64, sigma=1.0)
+    u0 = torch.from_numpy(synth.wavefunction_sum(n, n, L, L, seed=3, count=8)).cuda()
+    w = torch.from_numpy(synth.normal_field(n, n, seed=4)).cuda()
+
+    def loss_of(u):
+        return (w * (u.real ** 2 + u.imag ** 2)).sum() + (w * u.real).sum()
+
+    grads = []
+    for ck in (5, 0):
+        u = u0.clone().requires_grad_(True)
+        loss_of(evolve(u, steps, ds, solver, tau, 1.0, -1.0, checkpoint_every=ck, scheme="yoshida")).backward()
+        grads.append(u.grad.clone())
+    assert torch.allclose(grads[0], grads[1], rtol=0, atol=1e-12 * float(grads[1].abs().max()))
+    gen = torch.Generator(device="cpu").manual_seed(11)
+    d = torch.complex(torch.randn(n, n, generator=gen, dtype=torch.float64),
+                      torch.randn(n, n, generator=gen, dtype=torch.float64)).cuda()
+    an = float((grads[1].real * d.real + grads[1].imag * d.imag).sum())
+    h = 1e-6
+    with torch.no_grad():
+        fp = float(loss_of(evolve(u0 + h * d, steps, ds, solver, tau, 1.0, -1.0, scheme="yoshida")))
+        fm = float(loss_of(evolve(u0 - h * d, steps, ds, solver, tau, 1.0, -1.0, scheme="yoshida")))
+    assert abs((fp - fm) / (2 * h) - an) <= 1e-6 * abs(an)
+    solver.close()
+    ds.close()
+
+
+def _lump_phi(X, Y, t):
+    """Case I of Example 3: the exact potential of the moving lump."""
+    d = (X + 1.0) ** 2 + (Y + 4.0 * t) ** 2 + 1.0
+    return -2.0 * ((Y + 4.0 * t) ** 2 - X * (X + 2.0)) / (d * d)
+
+
+def _lump_errors(L, h, standard):
+    """Arkadiev's moving lump (alpha = 1, beta = -1) from t = 0 to T = 0.4 with
+    Yoshida steps of 1e-3 (the paper's integrator and step); relative l2 errors
+    of u(T) and of Phi computed from |u(T)|^2."""
+    from paper_1409_2014_gb300 import Plan
+    from paper_1409_2014_gb300.ds import DSPlan, evolve
+
+    n = int(round(2 * L / h))
+    x = oracle.grid_axis(n, L)
+    X, Y = np.meshgrid(x, x)
+    if standard:
+        solver = Plan(n, lx=L, partition="none", precision="fp64")
+    else:
+        P = min(6.0 * 12.0 / L, 0.5 * math.pi / h)
+        solver = Plan(n, lx=L, cut_radius=P, sigma=P / 6.0, n_r=64, n_theta=128, precision="fp64")
+    ds = DSPlan(n, lx=L, precision="fp64")
+    with torch.no_grad():
+        u = evolve(torch.from_numpy(D.arkadiev_lump(X, Y, 0.0)).cuda(), 400, ds, solver, 1e-3, 1.0, -1.0,
+                   scheme="yoshida")
+        phi = solver.solve(ds.abs2(u)).cpu().numpy()
+    u = u.cpu().numpy()
+    solver.close()
+    ds.close()
+    ex_u, ex_phi = D.arkadiev_lump(X, Y, 0.4), _lump_phi(X, Y, 0.4)
+    return (float(np.linalg.norm(u - ex_u) / np.linalg.norm(ex_u)),
+            float(np.linalg.norm(phi - ex_phi) / np.linalg.norm(ex_phi)))
+
+
+@pytest.mark.parametrize("L,h,pu,pphi", read_golden("table7_ds_case1_fft.txt"))
+def test_table7_moving_lump_standard_fft_solver(L, h, pu, pphi):
+    eu, ephi = _lump_errors(L, h, standard=True)
+    assert abs(eu / pu - 1.0) <= 0.006 and abs(ephi / pphi - 1.0) <= 0.006, (eu, ephi)
+
+
+@pytest.mark.parametrize("L,h,pu,pphi", read_golden("table8_ds_case1_nufft_full.txt"))
+def test_table8_moving_lump_split_solver(L, h, pu, pphi):
+    eu, ephi = _lump_errors(L, h, standard=False)
+    assert abs(eu / pu - 1.0) <= 0.006 and abs(ephi / pphi - 1.0) <= 0.006, (eu, ephi)
