@@ -20,18 +20,21 @@ from ._abi import (  # noqa: F401
 
 _PREC = {"fp64": DSNU_FP64, "mixed": DSNU_MIXED}
 _PART = {"gauss": DSNU_PARTITION_GAUSS, "sharp": DSNU_PARTITION_SHARP, "none": DSNU_PARTITION_NONE}
+_RADIAL = {"legendre": _abi.DSNU_RADIAL_LEGENDRE, "jacobi": _abi.DSNU_RADIAL_JACOBI}
 
 
 def make_params(nx, ny, lx, ly, cut_radius, n_r, n_theta, sigma=0.0, kernel_width=0,
-                precision="fp64", partition="gauss") -> dsnu_params:
+                precision="fp64", partition="gauss", radial="legendre") -> dsnu_params:
     """partition "none" selects the standard periodic FFT solver (no split, no
-    padding: pad_factor 1); the polar parameters are then ignored."""
+    padding: pad_factor 1); the polar parameters are then ignored.  radial:
+    "legendre" or "jacobi" (the radial rule of the polar quadrature)."""
     standard = partition == "none"
     return dsnu_params(nx=int(nx), ny=int(ny), lx=float(lx), ly=float(ly),
                        cut_radius=float(cut_radius or 0.0), sigma=float(sigma), n_r=int(n_r or 0),
                        n_theta=int(n_theta or 0), kernel_width=int(kernel_width),
                        pad_factor=1 if standard else 2,
-                       precision=_PREC[precision], partition=_PART[partition])
+                       precision=_PREC[precision], partition=_PART[partition],
+                       radial_rule=_RADIAL[radial], reserved=0)
 
 
 class Plan:
@@ -41,7 +44,8 @@ class Plan:
     Phi (float64, same shape), enqueued on the current torch stream."""
 
     def __init__(self, nx, ny=None, lx=None, ly=None, cut_radius=None, n_r=None, n_theta=None,
-                 sigma=0.0, kernel_width=0, precision="fp64", partition="gauss", device=None):
+                 sigma=0.0, kernel_width=0, precision="fp64", partition="gauss", radial="legendre",
+                 device=None, params=None):
         import torch
 
         ny = nx if ny is None else ny
@@ -52,8 +56,8 @@ class Plan:
         if dev.index is None:
             dev = torch.device("cuda", torch.cuda.current_device())
         self.device = dev
-        self.params = make_params(nx, ny, lx, ly, cut_radius, n_r, n_theta, sigma, kernel_width,
-                                  precision, partition)
+        self.params = params if params is not None else make_params(
+            nx, ny, lx, ly, cut_radius, n_r, n_theta, sigma, kernel_width, precision, partition, radial)
         self.shape = (int(ny), int(nx))
         self._handle = None
         with torch.cuda.device(self.device):
@@ -63,6 +67,16 @@ class Plan:
             self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
             dsnu_set_workspace(self._handle, self.workspace.data_ptr(), self.workspace.numel())
         self.info = dsnu_plan_get_info(self._handle)
+
+    @classmethod
+    def auto(cls, nx, ny=None, lx=None, ly=None, eps=1e-12, precision="fp64", device=None):
+        """A plan whose polar part is chosen for the target accuracy eps
+        (dsnu_params_auto: sigma = 12/min(l), P = sigma sqrt(ln 1/eps),
+        Gauss-Jacobi radial rule, node counts from P sqrt(lx^2 + ly^2))."""
+        ny = nx if ny is None else ny
+        ly = lx if ly is None else ly
+        prm = _abi.dsnu_params_auto(nx, ny, lx, ly, eps, _PREC[precision])
+        return cls(nx, ny, lx, ly, precision=precision, device=device, params=prm)
 
     @property
     def handle(self) -> int:

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libdsnufft.so")
 DSNU_OK, DSNU_EINVAL, DSNU_ENOMEM, DSNU_ECUDA, DSNU_ETIMEOUT, DSNU_EUNSUPPORTED = range(6)
 DSNU_FP64, DSNU_MIXED = 0, 1
 DSNU_PARTITION_GAUSS, DSNU_PARTITION_SHARP, DSNU_PARTITION_NONE = 0, 1, 2
+DSNU_RADIAL_LEGENDRE, DSNU_RADIAL_JACOBI = 0, 1
 
 STATUS_NAMES = {0: "DSNU_OK", 1: "DSNU_EINVAL", 2: "DSNU_ENOMEM", 3: "DSNU_ECUDA",
                 4: "DSNU_ETIMEOUT", 5: "DSNU_EUNSUPPORTED"}
@@ -28,7 +29,7 @@ EXPORTED = [
     "dsnu_ds_plan_create", "dsnu_ds_set_linear_step", "dsnu_ds_linear", "dsnu_ds_abs2",
     "dsnu_ds_nonlinear", "dsnu_ds_nonlinear_vjp", "dsnu_ds_nonlinear_vjp_finish", "dsnu_ds_plan_destroy",
     "dsnu_batch_create", "dsnu_batch_workspace_bytes", "dsnu_batch_bind", "dsnu_batch_capture_graph",
-    "dsnu_batch_solve", "dsnu_batch_destroy",
+    "dsnu_batch_solve", "dsnu_batch_destroy", "dsnu_radial_nodes", "dsnu_params_auto",
 ]
 
 
@@ -40,6 +41,7 @@ class dsnu_params(ctypes.Structure):
         ("n_r", ctypes.c_int32), ("n_theta", ctypes.c_int32),
         ("kernel_width", ctypes.c_int32), ("pad_factor", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("partition", ctypes.c_int32),
+        ("radial_rule", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -105,6 +107,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dsnu_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int)]
     lib.dsnu_profile_end.restype = st
+    lib.dsnu_radial_nodes.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.dsnu_radial_nodes.restype = st
+    lib.dsnu_params_auto.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_int32, ctypes.POINTER(dsnu_params)]
+    lib.dsnu_params_auto.restype = st
     lib.dsnu_stage_count.argtypes = []
     lib.dsnu_stage_count.restype = ctypes.c_int32
     lib.dsnu_stage_name.argtypes = [ctypes.c_int32]
@@ -213,6 +221,21 @@ def dsnu_profile_end(plan: int):
     _check(load().dsnu_profile_end(ctypes.c_void_p(plan), arr, n, ctypes.byref(cnt)),
            "dsnu_profile_end")
     return list(arr), cnt.value
+
+
+def dsnu_radial_nodes(n_r: int, rule: int, cut_radius: float):
+    """(r, w) lists: nodes in (0, P) and weights for int_0^P f(r) r dr (host only)."""
+    r = (ctypes.c_double * int(n_r))()
+    w = (ctypes.c_double * int(n_r))()
+    _check(load().dsnu_radial_nodes(int(n_r), int(rule), float(cut_radius), r, w), "dsnu_radial_nodes")
+    return list(r), list(w)
+
+
+def dsnu_params_auto(nx: int, ny: int, lx: float, ly: float, eps: float, precision: int) -> dsnu_params:
+    out = dsnu_params()
+    _check(load().dsnu_params_auto(int(nx), int(ny), float(lx), float(ly), float(eps), int(precision),
+                                   ctypes.byref(out)), "dsnu_params_auto")
+    return out
 
 
 def dsnu_stage_count() -> int:

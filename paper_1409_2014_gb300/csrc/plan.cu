@@ -81,6 +81,84 @@ static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w
   }
 }
 
+// P_n and P_{n-1} of the Jacobi polynomials P^{(a,b)} with a = 0, b = 1 at t,
+// from the three-term recurrence
+//   2(k+1)(k+a+b+1)(2k+a+b) P_{k+1}
+//     = (2k+a+b+1)[(2k+a+b+2)(2k+a+b) t + a^2 - b^2] P_k - 2(k+a)(k+b)(2k+a+b+2) P_{k-1},
+// P_0 = 1, P_1 = (3t - 1)/2.
+static void jacobi01(int n, double t, double* pn, double* pn1) {
+  double p0 = 1.0, p1 = 0.5 * (3.0 * t - 1.0);
+  if (n == 0) {
+    *pn = 1.0;
+    *pn1 = 0.0;
+    return;
+  }
+  for (int k = 1; k < n; ++k) {
+    const double c1 = 2.0 * (k + 1) * (k + 2) * (2.0 * k + 1);
+    const double c2 = -(2.0 * k + 2);
+    const double c3 = (2.0 * k + 1) * (2.0 * k + 2) * (2.0 * k + 3);
+    const double c4 = 2.0 * k * (k + 1) * (2.0 * k + 3);
+    const double p2 = ((c2 + c3 * t) * p1 - c4 * p0) / c1;
+    p0 = p1;
+    p1 = p2;
+  }
+  *pn = p1;
+  *pn1 = p0;
+}
+
+// Gauss-Jacobi nodes (ascending) and weights on [-1, 1] for the weight
+// function (1 + t): Newton on P_n^{(0,1)} with the roots already found divided
+// out, started from cos(pi (i - 1/4)/(n + 1)); the derivative from
+//   (2n+1)(1 - t^2) P_n' = n[-1 - (2n+1) t] P_n + 2n(n+1) P_{n-1},
+// the weights 4 / ((1 - t^2) P_n'(t)^2).
+static void gauss_jacobi01(int n, std::vector<double>& x, std::vector<double>& w) {
+  std::vector<double> roots;
+  auto deriv = [n](double t, double pn, double pn1) {
+    return (n * (-1.0 - (2.0 * n + 1) * t) * pn + 2.0 * n * (n + 1) * pn1) / ((2.0 * n + 1) * (1.0 - t * t));
+  };
+  for (int i = 1; i <= n; ++i) {
+    double z = std::cos(M_PI * (i - 0.25) / (n + 1.0));
+    for (int it = 0; it < 200; ++it) {
+      double pn, pn1;
+      jacobi01(n, z, &pn, &pn1);
+      double defl = 0.0;
+      for (double r : roots) defl += 1.0 / (z - r);
+      const double dz = pn / (deriv(z, pn, pn1) - pn * defl);
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    roots.push_back(z);
+  }
+  std::sort(roots.begin(), roots.end());
+  x = roots;
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double pn, pn1;
+    jacobi01(n, x[i], &pn, &pn1);
+    const double d = deriv(x[i], pn, pn1);
+    w[i] = 4.0 / ((1.0 - x[i] * x[i]) * d * d);
+  }
+}
+
+// Radial nodes r_i in (0, P) (ascending) and weights W_i with
+// sum_i W_i f(r_i) ~ int_0^P f(r) r dr (the polar Jacobian r, Sec. 2.1):
+// Gauss-Legendre mapped to [0, P] with r multiplied into the weight, or the
+// Gauss-Jacobi(0, 1) rule whose weight function is that Jacobian
+// (r = P (1 + t)/2, r dr = (P/2)^2 (1 + t) dt).
+static void radial_nodes(int n, int rule, double P, std::vector<double>& r, std::vector<double>& w) {
+  std::vector<double> t, v;
+  if (rule == DSNU_RADIAL_JACOBI) {
+    gauss_jacobi01(n, t, v);
+    for (double& x : v) x *= 0.25 * P * P;
+  } else {
+    gauss_legendre(n, t, v);
+    for (int i = 0; i < n; ++i) v[i] *= 0.5 * P * (0.5 * P * (t[i] + 1.0));
+  }
+  r.resize(n);
+  for (int i = 0; i < n; ++i) r[i] = 0.5 * P * (t[i] + 1.0);
+  w = v;
+}
+
 static double es_kernel(double z, int w, double beta) {
   const double t = 2.0 * z / w;
   const double u = 1.0 - t * t;
@@ -299,8 +377,9 @@ static dsnu_status setup_spread(dsnu_plan_s* P, const std::vector<int2>& q0, con
   int dev = 0;
   cudaGetDevice(&dev);
   char key[256];
-  std::snprintf(key, sizeof(key), "%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|%d|%d", dev, p.nx, p.ny, p.lx, p.ly,
-                p.cut_radius, p.sigma, p.n_r, p.n_theta, p.kernel_width, p.precision, p.partition);
+  std::snprintf(key, sizeof(key), "%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|%d|%d|%d", dev, p.nx, p.ny, p.lx,
+                p.ly, p.cut_radius, p.sigma, p.n_r, p.n_theta, p.kernel_width, p.precision, p.partition,
+                p.radial_rule);
   const char* env = std::getenv("DSNU_AUTOTUNE");
   const bool tune = !(env && env[0] == '0');
   int choice = 0;
@@ -360,20 +439,19 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   const double sigma = g.sigma, beta = g.beta;
 
   // polar nodes and weights
-  std::vector<double> gx, gw;
-  gauss_legendre(p.n_r, gx, gw);
+  std::vector<double> rn, rw;
+  radial_nodes(p.n_r, p.radial_rule, p.cut_radius, rn, rw);
   const int nn = p.n_r * p.n_theta;
   std::vector<double> kx(nn), ky(nn), D(nn);
   for (int i = 0; i < p.n_r; ++i) {
-    const double r = 0.5 * p.cut_radius * (gx[i] + 1.0);
-    const double wr = 0.5 * p.cut_radius * gw[i];
+    const double r = rn[i];
     const double pr = g.sharp ? 1.0 : std::exp(-r * r / (sigma * sigma));
     for (int j = 0; j < p.n_theta; ++j) {
       const double th = 2.0 * M_PI * j / p.n_theta;
       const double c = std::cos(th), s = std::sin(th);
       kx[i * p.n_theta + j] = r * c;
       ky[i * p.n_theta + j] = r * s;
-      D[i * p.n_theta + j] = -(r * wr * (2.0 * M_PI / p.n_theta) * c * c * pr) / (4.0 * M_PI * M_PI);
+      D[i * p.n_theta + j] = -(rw[i] * (2.0 * M_PI / p.n_theta) * c * c * pr) / (4.0 * M_PI * M_PI);
     }
   }
 
@@ -575,6 +653,8 @@ dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan*
     if (p.n_r < 1 || p.n_r > 4096) return fail(DSNU_EINVAL, "n_r must be in [1, 4096]");
     if (p.n_theta < 2 || (p.n_theta & 1) || p.n_theta > 65536)
       return fail(DSNU_EINVAL, "n_theta must be even, >= 2");
+    if (p.radial_rule != DSNU_RADIAL_LEGENDRE && p.radial_rule != DSNU_RADIAL_JACOBI)
+      return fail(DSNU_EINVAL, "unknown radial_rule");
     if (p.kernel_width == 0) p.kernel_width = (p.precision == DSNU_FP64) ? 15 : 8;
     if (p.kernel_width < 2 || p.kernel_width > 16) return fail(DSNU_EINVAL, "kernel_width must be in [2, 16]");
     if (p.sigma == 0.0) p.sigma = p.cut_radius / 6.0;
@@ -747,6 +827,57 @@ dsnu_status dsnu_profile_end(dsnu_plan plan, double* stage_ms, int n_stages, int
   if (n_solves) *n_solves = plan->prof_used;
   free_profile(plan);
   return st;
+}
+
+dsnu_status dsnu_radial_nodes(int32_t n_r, int32_t rule, double cut_radius, double* r, double* w) {
+  if (n_r < 1 || n_r > 4096 || !r || !w || !(cut_radius > 0.0) || !std::isfinite(cut_radius))
+    return fail(DSNU_EINVAL, "n_r in [1, 4096], cut_radius > 0 and output arrays required");
+  if (rule != DSNU_RADIAL_LEGENDRE && rule != DSNU_RADIAL_JACOBI) return fail(DSNU_EINVAL, "unknown radial rule");
+  std::vector<double> rn, rw;
+  radial_nodes(n_r, rule, cut_radius, rn, rw);
+  for (int i = 0; i < n_r; ++i) {
+    r[i] = rn[i];
+    w[i] = rw[i];
+  }
+  return DSNU_OK;
+}
+
+dsnu_status dsnu_params_auto(int32_t nx, int32_t ny, double lx, double ly, double eps, int32_t precision,
+                             dsnu_params* out) {
+  if (!out) return fail(DSNU_EINVAL, "NULL out");
+  if (!is_pow2(nx) || !is_pow2(ny) || nx < 16 || ny < 16 || nx > 4096 || ny > 4096)
+    return fail(DSNU_EINVAL, "nx, ny must be powers of two in [16, 4096]");
+  if (!(lx > 0.0) || !(ly > 0.0) || !std::isfinite(lx) || !std::isfinite(ly))
+    return fail(DSNU_EINVAL, "lx, ly must be positive and finite");
+  if (precision != DSNU_FP64 && precision != DSNU_MIXED) return fail(DSNU_EINVAL, "unknown precision");
+  if (!(eps > 0.0) || !(eps < 1.0)) return fail(DSNU_EINVAL, "eps must be in (0, 1)");
+  eps = std::min(std::max(eps, precision == DSNU_MIXED ? 1e-7 : 1e-15), 1e-2);
+  const double sigma = 12.0 / std::min(lx, ly);             // sigma L = 12
+  const double c = sigma * std::sqrt(std::log(1.0 / eps));  // p(c) = eps
+  const double cR = c * std::sqrt(lx * lx + ly * ly);       // largest phase of e^{i k.x} on the disk
+  const int n_theta = 4 * int(std::ceil((cR + 16.0) / 4.0));
+  const int n_r = 8 * int(std::ceil((0.5 * cR + 4.0) / 8.0));
+  const int w = (precision == DSNU_FP64) ? 15 : 8;
+  const double hx = 2.0 * lx / nx, hy = 2.0 * ly / ny;
+  if (c * hx + w * M_PI / (2.0 * nx) >= M_PI || c * hy + w * M_PI / (2.0 * ny) >= M_PI)
+    return fail(DSNU_EINVAL, "grid too coarse for this domain: the disk radius 12 sqrt(ln 1/eps)/min(lx, ly) "
+                             "plus the ES stencil exceeds the padded frequency grid");
+  dsnu_params p{};
+  p.nx = nx;
+  p.ny = ny;
+  p.lx = lx;
+  p.ly = ly;
+  p.cut_radius = c;
+  p.sigma = sigma;
+  p.n_r = n_r;
+  p.n_theta = n_theta;
+  p.kernel_width = 0;
+  p.pad_factor = 2;
+  p.precision = precision;
+  p.partition = DSNU_PARTITION_GAUSS;
+  p.radial_rule = DSNU_RADIAL_JACOBI;
+  *out = p;
+  return DSNU_OK;
 }
 
 int32_t dsnu_stage_count(void) { return kStages; }

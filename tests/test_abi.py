@@ -37,12 +37,63 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(_abi.EXPORTED) <= set(names)
 
 
-def test_struct_layout_matches_header():
-    assert ctypes.sizeof(_abi.dsnu_params) == 64
+def test_struct_layout_matches_header(tmp_path):
+    """ctypes layouts equal the C compiler's for the header's structs."""
+    import shutil
+    import subprocess
+
+    assert ctypes.sizeof(_abi.dsnu_params) == 72
     assert _abi.dsnu_params.lx.offset == 8
     assert _abi.dsnu_params.n_r.offset == 40
     assert _abi.dsnu_params.partition.offset == 60
+    assert _abi.dsnu_params.radial_rule.offset == 64
     assert ctypes.sizeof(_abi.dsnu_plan_info) == 56
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    checks = []
+    for struct, cls in (("dsnu_params", _abi.dsnu_params), ("dsnu_plan_info", _abi.dsnu_plan_info),
+                        ("dsnu_ds_params", _abi.dsnu_ds_params)):
+        checks.append(f'printf("{struct} sizeof %zu\\n", sizeof({struct}));')
+        for name, _ in cls._fields_:
+            checks.append(f'printf("{struct} {name} %zu\\n", offsetof({struct}, {name}));')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "dsnufft.h"\nint main(void) {\n'
+                   + "\n".join(checks) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line.strip()}
+    for struct, cls in (("dsnu_params", _abi.dsnu_params), ("dsnu_plan_info", _abi.dsnu_plan_info),
+                        ("dsnu_ds_params", _abi.dsnu_ds_params)):
+        assert got[(struct, "sizeof")] == ctypes.sizeof(cls), struct
+        for name, _ in cls._fields_:
+            assert got[(struct, name)] == getattr(cls, name).offset, (struct, name)
+
+
+@pytest.mark.parametrize("rule,name", [(0, "legendre"), (1, "jacobi")])
+@pytest.mark.parametrize("n_r", [1, 2, 7, 33, 64, 200])
+def test_library_radial_rule_matches_oracle(lib, rule, name, n_r):
+    """dsnu_radial_nodes (the library's own Newton solvers) equals the oracle's
+    rule (numpy's Gauss-Legendre table, scipy's Gauss-Jacobi table)."""
+    import numpy as np
+
+    import oracle as O
+
+    P = 5.5
+    r, w = _abi.dsnu_radial_nodes(n_r, rule, P)
+    ro, wo = O.radial_rule(O.OracleParams(nx=8, ny=8, lx=1, ly=1, cut_radius=P, n_r=n_r, n_theta=4, radial=name))
+    assert np.abs(np.array(r) - ro).max() <= 1e-14 * P
+    # numpy's Gauss-Legendre weights lose accuracy with n (3.9e-13 of the largest
+    # weight at n = 200 against a 40-digit evaluation; the library's 4.9e-15)
+    tol = 1e-13 if n_r <= 64 else 1e-12
+    assert np.abs(np.array(w) - wo).max() <= tol * np.abs(wo).max()
+
+
+def test_library_radial_rule_rejects_bad_input(lib):
+    for args in ((0, 0, 1.0), (4097, 0, 1.0), (4, 2, 1.0), (4, 0, 0.0), (4, 1, float("nan"))):
+        with pytest.raises(_abi.DsnuError):
+            _abi.dsnu_radial_nodes(*args)
 
 
 def _params(**kw):

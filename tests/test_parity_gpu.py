@@ -68,6 +68,19 @@ def test_small_grids_vs_oracle(case, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", [CASES[0], CASES[3], CASES[5]])
+def test_gauss_jacobi_radial_rule_vs_oracle(case, prec):
+    """The Gauss-Jacobi(0,1) radial rule of Sec. 2.1 (weight = the Jacobian r)."""
+    nx, ny, lx, ly, P, nr, nt, sg = case
+    rho = synth.density_abs2(nx, ny, lx, ly, seed=nx + ny + 1, count=6)
+    op = oracle.OracleParams(nx=nx, ny=ny, lx=lx, ly=ly, cut_radius=P, n_r=nr, n_theta=nt, sigma=sg,
+                             radial="jacobi")
+    ref = oracle.solve(rho, op)
+    got = gpu_solve(rho, prec, lx=lx, ly=ly, cut_radius=P, n_r=nr, n_theta=nt, sigma=sg, radial="jacobi")
+    assert rel_linf(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_config1_closed_form(prec):
     """128^2 on [-16,16)^2, rho = exp(-r^2), P = 4, 32 x 64 nodes."""
     n, L = 128, 16.0
@@ -81,10 +94,11 @@ def test_config1_closed_form(prec):
     assert rel_linf(got, oracle.gaussian_potential(X, Y)) < 1e-6
 
 
-def test_config1_resolved_closed_form_fp64():
+@pytest.mark.parametrize("radial", ["legendre", "jacobi"])
+def test_config1_resolved_closed_form_fp64(radial):
     n, L = 128, 16.0
     rho = synth.isotropic_gaussian(n, n, L, L)
-    got = gpu_solve(rho, "fp64", lx=L, cut_radius=4.0, n_r=48, n_theta=96, sigma=2 / 3)
+    got = gpu_solve(rho, "fp64", lx=L, cut_radius=4.0, n_r=48, n_theta=96, sigma=2 / 3, radial=radial)
     x = oracle.grid_axis(n, L)
     X, Y = np.meshgrid(x, x)
     assert rel_linf(got, oracle.gaussian_potential(X, Y)) < 1e-13
