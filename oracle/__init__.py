@@ -27,7 +27,9 @@ from .potential import (  # noqa: F401
     radial_rule,
     polar_weights,
     partition,
+    multiplier,
     multiplier_high,
+    DS_MULTIPLIER,
     i1_padded_fft,
     i1_padded_fft_adjoint,
     rho_hat_direct,
@@ -40,6 +42,9 @@ from .potential import (  # noqa: F401
 from .closed_forms import (  # noqa: F401
     gaussian_potential,
     gaussian_i2_exact,
+    gaussian_potential_alpha0,
+    gaussian_coulomb,
+    gaussian_abs_k,
     paper_gaussian_density,
     paper_gaussian_potential,
     arkadiev_density,

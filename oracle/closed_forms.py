@@ -14,6 +14,18 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   untruncated disk; the disk |w| <= P drops a part of relative size
   exp(-l^2 P^2 / 4)).
 * Arkadiev's rational pair of Example 2 (Sec. 3.1).
+* Other multipliers of the family |w|^alpha (a0 + ac cos 2theta + as sin 2theta)
+  (the Remark of Sec. 2.2), for rho = exp(-r^2), rho_hat = pi exp(-|w|^2/4):
+  - alpha = 0: a0 rho + (ac cos 2phi + as sin 2phi) f(r), where f is the
+    cos 2phi part above (a rotation by 45 degrees turns cos 2theta into
+    sin 2theta in both spaces);
+  - 2 pi/|w| (the 2D transform of the 3D Coulomb kernel 1/|x|):
+    Phi = (2 pi)^-2 int 2 pi^2 e^{-k^2/4}/k e^{i w.x} dw = pi int_0^inf e^{-k^2/4} J0(k r) dk
+        = pi^{3/2} e^{-r^2/2} I0(r^2/2);
+  - |w|: Phi = 1/2 int_0^inf k^2 e^{-k^2/4} J0(k r) dk
+        = sqrt(pi) e^{-r^2/2} [(1 - r^2) I0(r^2/2) + r^2 I1(r^2/2)]
+  (both integrals from int_0^inf e^{-a k^2} J0(b k) dk = (1/2) sqrt(pi/a)
+  e^{-b^2/(8a)} I0(b^2/(8a)) and its derivative in a).
 """
 
 from __future__ import annotations
@@ -21,6 +33,7 @@ from __future__ import annotations
 import math
 
 import numpy as np
+import scipy.special
 
 
 def _f2(s: np.ndarray) -> np.ndarray:
@@ -48,6 +61,26 @@ def gaussian_potential(x: np.ndarray, y: np.ndarray) -> np.ndarray:
     y = np.asarray(y, dtype=np.float64)
     s = x * x + y * y
     return -0.5 * (np.exp(-s) + (x * x - y * y) * _f2(s))
+
+
+def gaussian_potential_alpha0(x: np.ndarray, y: np.ndarray, a0: float, ac: float, as_: float) -> np.ndarray:
+    """Phi for rho = exp(-r^2) and m = a0 + ac cos 2theta + as sin 2theta."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    s = x * x + y * y
+    return a0 * np.exp(-s) + (ac * (x * x - y * y) + as_ * 2.0 * x * y) * _f2(s)
+
+
+def gaussian_coulomb(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Phi for rho = exp(-r^2) and m = 2 pi/|w|: pi^{3/2} e^{-r^2/2} I0(r^2/2)."""
+    s = np.asarray(x, dtype=np.float64) ** 2 + np.asarray(y, dtype=np.float64) ** 2
+    return math.pi ** 1.5 * scipy.special.i0e(0.5 * s)
+
+
+def gaussian_abs_k(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Phi for rho = exp(-r^2) and m = |w|."""
+    s = np.asarray(x, dtype=np.float64) ** 2 + np.asarray(y, dtype=np.float64) ** 2
+    return math.sqrt(math.pi) * ((1.0 - s) * scipy.special.i0e(0.5 * s) + s * scipy.special.i1e(0.5 * s))
 
 
 def gaussian_i2_exact(x: np.ndarray, y: np.ndarray, sigma: float) -> np.ndarray:

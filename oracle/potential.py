@@ -62,6 +62,9 @@ class OracleParams:
     pad: int = 2
     partition: str = "gauss"
     radial: str = "legendre"  # "legendre" (Jacobian r in the weight) or "jacobi" (weight (1+t), Sec. 2.1)
+    # Fourier multiplier m(k) = |k|^alpha (a0 + ac cos 2theta + as sin 2theta), theta = arg k, as
+    # (alpha, a0, ac, as); the default (0, -1/2, -1/2, 0) is -cos^2 theta = -k_x^2/|k|^2 (eq. Disct_Fourier)
+    multiplier: tuple = (0, -0.5, -0.5, 0.0)
 
     @property
     def hx(self) -> float:
@@ -93,13 +96,30 @@ def partition(w2: np.ndarray, p: OracleParams) -> np.ndarray:
     raise ValueError(f"unknown partition {p.partition!r}")
 
 
-def multiplier_high(wx: np.ndarray, wy: np.ndarray, p: OracleParams) -> np.ndarray:
-    """m1 = -w_x^2/|w|^2 (1 - p(w)), with m1(0) = 0 (eq. SubInt1; the value at
-    the origin is the rho_hat(0) = 0 convention of Sec. 2.1)."""
+DS_MULTIPLIER = (0, -0.5, -0.5, 0.0)
+
+
+def multiplier(wx: np.ndarray, wy: np.ndarray, p: OracleParams) -> np.ndarray:
+    """m(w) with m(0) = 0 (the rho_hat(0) = 0 convention of Sec. 2.1).  The DS
+    multiplier is -w_x^2/|w|^2 (eq. Disct_Fourier); the Remark of Sec. 2.2
+    applies the method to any multiplier known analytically, here
+    |w|^alpha (a0 + ac cos 2theta + as sin 2theta) with
+    cos 2theta = (w_x^2 - w_y^2)/|w|^2 and sin 2theta = 2 w_x w_y/|w|^2."""
     w2 = wx * wx + wy * wy
     with np.errstate(divide="ignore", invalid="ignore"):
-        m = np.where(w2 > 0, -(wx * wx) / w2, 0.0)
-    return m * (1.0 - partition(w2, p))
+        if tuple(p.multiplier) == DS_MULTIPLIER:
+            m = -(wx * wx) / w2
+        else:
+            alpha, a0, ac, as_ = p.multiplier
+            ang = a0 + (ac * (wx * wx - wy * wy) + as_ * 2.0 * wx * wy) / w2
+            m = np.power(w2, 0.5 * alpha) * ang
+        return np.where(w2 > 0, m, 0.0)
+
+
+def multiplier_high(wx: np.ndarray, wy: np.ndarray, p: OracleParams) -> np.ndarray:
+    """m1 = m (1 - p(w)) (eq. SubInt1), m1(0) = 0."""
+    w2 = wx * wx + wy * wy
+    return multiplier(wx, wy, p) * (1.0 - partition(w2, p))
 
 
 def _omega_axis(m_pts: int, h: float) -> np.ndarray:
@@ -179,12 +199,18 @@ def polar_nodes(p: OracleParams):
 def polar_weights(p: OracleParams) -> np.ndarray:
     """D_j = -(2 pi)^-2 W_r (2 pi/N_theta) cos^2(theta) p(r): the weights of
     eq. I2PolarDisc with the Jacobian r (inside W_r) and the (2 pi)^-2 of the
-    angular frequency convention written in."""
+    angular frequency convention written in.  For another multiplier
+    r^alpha (a0 + ac cos 2theta + as sin 2theta) replaces -cos^2(theta)."""
     _, _, r, w_rad, theta = polar_nodes(p)
     w_theta = TWO_PI / p.n_theta
-    radial = w_rad * partition(r * r, p)
-    ang = np.cos(theta) ** 2 * w_theta
-    return (-(radial[:, None] * ang[None, :]) / TWO_PI**2).ravel()
+    if tuple(p.multiplier) == DS_MULTIPLIER:
+        radial = w_rad * partition(r * r, p)
+        ang = -np.cos(theta) ** 2 * w_theta
+    else:
+        alpha, a0, ac, as_ = p.multiplier
+        radial = w_rad * np.power(r, float(alpha)) * partition(r * r, p)
+        ang = (a0 + ac * np.cos(2.0 * theta) + as_ * np.sin(2.0 * theta)) * w_theta
+    return ((radial[:, None] * ang[None, :]) / TWO_PI**2).ravel()
 
 
 def _node_chunks(n_nodes: int, width: int, chunk: int):
@@ -277,10 +303,10 @@ def solve_adjoint(g: np.ndarray, p: OracleParams) -> np.ndarray:
     return i1_padded_fft_adjoint(g, p) + i2t
 
 
-def standard_fft_solve(rho: np.ndarray, lx: float, ly: float) -> np.ndarray:
+def standard_fft_solve(rho: np.ndarray, lx: float, ly: float, multiplier=DS_MULTIPLIER) -> np.ndarray:
     """The standard periodic FFT solver of Sec. 2.1 (no split, no padding,
     Phi_hat(0) = 0), i.e. I1 with p = 0 and kappa = 1.  Used for Table 1."""
     ny, nx = rho.shape
     p = OracleParams(nx=nx, ny=ny, lx=lx, ly=ly, cut_radius=1.0, n_r=1,
-                     n_theta=4, pad=1, partition="none")
+                     n_theta=4, pad=1, partition="none", multiplier=tuple(multiplier))
     return i1_padded_fft(rho, p)
