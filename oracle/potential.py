@@ -111,7 +111,12 @@ def multiplier(wx: np.ndarray, wy: np.ndarray, p: OracleParams) -> np.ndarray:
             m = -(wx * wx) / w2
         else:
             alpha, a0, ac, as_ = p.multiplier
-            ang = a0 + (ac * (wx * wx - wy * wy) + as_ * 2.0 * wx * wy) / w2
+            # the Nyquist frequency of an axis stands for both +K and -K: the
+            # odd sin 2theta term is averaged over the aliases, i.e. dropped there
+            nyq = np.isclose(np.abs(wx), math.pi / p.hx, rtol=1e-12, atol=0.0) | \
+                np.isclose(np.abs(wy), math.pi / p.hy, rtol=1e-12, atol=0.0)
+            odd = np.where(nyq, 0.0, as_ * 2.0 * wx * wy)
+            ang = a0 + (ac * (wx * wx - wy * wy) + odd) / w2
             m = np.power(w2, 0.5 * alpha) * ang
         return np.where(w2 > 0, m, 0.0)
 

@@ -95,3 +95,22 @@ def test_generic_operator_is_symmetric():
     rhs = float(np.sum(O.solve(b, p) * a))
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
     assert _rel(O.solve_adjoint(a, p), O.solve(a, p)) < 1e-12
+
+
+def test_nyquist_alias_average_keeps_the_multiplier_even():
+    """With the sin 2theta term averaged over the +-K aliases of the Nyquist row
+    and column, m(-k) = m(k) on the whole discrete grid, so the full complex
+    inverse transform of m (1 - p) rho_hat of a real density is real (the
+    reading that fixes the otherwise ambiguous Nyquist value)."""
+    import oracle.potential as OP
+
+    n, L = 32, 8.0
+    rho = np.random.default_rng(5).standard_normal((n, n))
+    p = OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=3.0, sigma=0.5, n_r=8, n_theta=16,
+                     multiplier=(0, 0.3, 0.7, -0.2))
+    buf = np.zeros((2 * n, 2 * n))
+    buf[:n, :n] = rho
+    wx = OP._omega_axis(2 * n, p.hx)[None, :]
+    wy = OP._omega_axis(2 * n, p.hy)[:, None]
+    out = np.fft.ifft2(np.fft.fft2(buf) * O.multiplier_high(wx, wy, p))
+    assert np.abs(out.imag).max() <= 1e-15 * np.abs(out.real).max()
