@@ -96,6 +96,20 @@ typedef struct {
 
 typedef struct dsnu_plan_s* dsnu_plan;
 
+/* A Fourier multiplier of the family (the Remark of Sec. 2.2: the split
+ * applies to any multiplier given analytically)
+ *     m(k) = |k|^alpha (a0 + a_cos cos 2theta + a_sin sin 2theta),  theta = arg k,
+ * alpha in {-1, 0, 1}, m(0) = 0 in the I1 part.  The DS multiplier -k_x^2/|k|^2
+ * is (0, -1/2, -1/2, 0); 2 pi/|k| (alpha = -1, a0 = 2 pi) is the 2D
+ * transform of the 3D Coulomb kernel 1/|x|; |k| (alpha = 1) the half
+ * Laplacian.  The split needs m (1 - p) continuous at 0 (alpha > -2) and
+ * m p r smooth in polar coordinates (alpha >= -1). */
+typedef struct {
+  int32_t alpha;
+  int32_t reserved;  /* set to 0 */
+  double a0, a_cos, a_sin;
+} dsnu_multiplier;
+
 /* Build a plan: validates params, computes (FP64, on the host) the polar
  * Gauss nodes and weights, the ES kernel weights of every node, the
  * deconvolution and multiplier tables and the twiddle tables, bins the nodes
@@ -108,6 +122,16 @@ typedef struct dsnu_plan_s* dsnu_plan;
  * dsnu_plan_destroy); it does not own the workspace.
  * Errors: DSNU_EINVAL (bad params, *out untouched), DSNU_ENOMEM, DSNU_ECUDA. */
 dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan* out);
+
+/* dsnu_plan_create for another multiplier of the family above: the column
+ * pass of I1 (and of the standard solver) applies m (1 - p), the polar
+ * weights carry r^alpha (a0 + a_cos cos 2theta + a_sin sin 2theta) in place of
+ * -cos^2 theta.  mult == NULL is dsnu_plan_create.  The operator stays real and
+ * symmetric, so dsnu_solve_adjoint and the batch and no-alloc entry points
+ * apply unchanged.  Errors: those of dsnu_plan_create, and DSNU_EINVAL for
+ * alpha outside {-1, 0, 1} or non-finite coefficients. */
+dsnu_status dsnu_plan_create_multiplier(const dsnu_params* params, const dsnu_multiplier* mult, void* stream,
+                                        dsnu_plan* out);
 
 /* Bytes of device scratch one solve needs (intermediate spectra).  0 on a
  * NULL plan. */

@@ -41,11 +41,13 @@ class Plan:
     """A solver plan on one CUDA device with a torch-owned workspace.
 
     ``solve(rho)`` takes a contiguous float64 (ny, nx) CUDA tensor and returns
-    Phi (float64, same shape), enqueued on the current torch stream."""
+    Phi (float64, same shape), enqueued on the current torch stream.
+    ``multiplier=(alpha, a0, a_cos, a_sin)`` selects m(k) = |k|^alpha (a0 +
+    a_cos cos 2theta + a_sin sin 2theta) instead of the DS -k_x^2/|k|^2."""
 
     def __init__(self, nx, ny=None, lx=None, ly=None, cut_radius=None, n_r=None, n_theta=None,
                  sigma=0.0, kernel_width=0, precision="fp64", partition="gauss", radial="legendre",
-                 device=None, params=None):
+                 device=None, params=None, multiplier=None):
         import torch
 
         ny = nx if ny is None else ny
@@ -62,7 +64,13 @@ class Plan:
         self._handle = None
         with torch.cuda.device(self.device):
             stream = torch.cuda.current_stream(self.device).cuda_stream
-            self._handle = dsnu_plan_create(self.params, stream)
+            if multiplier is None:
+                self._handle = dsnu_plan_create(self.params, stream)
+            else:
+                alpha, a0, a_cos, a_sin = multiplier
+                self.multiplier = _abi.dsnu_multiplier(alpha=int(alpha), reserved=0, a0=float(a0),
+                                                       a_cos=float(a_cos), a_sin=float(a_sin))
+                self._handle = _abi.dsnu_plan_create_multiplier(self.params, self.multiplier, stream)
             nbytes = dsnu_workspace_bytes(self._handle)
             self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
             dsnu_set_workspace(self._handle, self.workspace.data_ptr(), self.workspace.numel())

@@ -30,6 +30,7 @@ EXPORTED = [
     "dsnu_ds_nonlinear", "dsnu_ds_nonlinear_vjp", "dsnu_ds_nonlinear_vjp_finish", "dsnu_ds_plan_destroy",
     "dsnu_batch_create", "dsnu_batch_workspace_bytes", "dsnu_batch_bind", "dsnu_batch_capture_graph",
     "dsnu_batch_solve", "dsnu_batch_destroy", "dsnu_radial_nodes", "dsnu_params_auto",
+    "dsnu_plan_create_multiplier",
 ]
 
 
@@ -42,6 +43,13 @@ class dsnu_params(ctypes.Structure):
         ("kernel_width", ctypes.c_int32), ("pad_factor", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("partition", ctypes.c_int32),
         ("radial_rule", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class dsnu_multiplier(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("a0", ctypes.c_double), ("a_cos", ctypes.c_double), ("a_sin", ctypes.c_double),
     ]
 
 
@@ -110,6 +118,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dsnu_radial_nodes.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.dsnu_radial_nodes.restype = st
+    lib.dsnu_plan_create_multiplier.argtypes = [ctypes.POINTER(dsnu_params), ctypes.POINTER(dsnu_multiplier), vp,
+                                                ctypes.POINTER(vp)]
+    lib.dsnu_plan_create_multiplier.restype = st
     lib.dsnu_params_auto.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_int32, ctypes.POINTER(dsnu_params)]
     lib.dsnu_params_auto.restype = st
@@ -160,6 +171,14 @@ def dsnu_plan_create(params: dsnu_params, stream: int = 0) -> int:
     out = ctypes.c_void_p()
     _check(load().dsnu_plan_create(ctypes.byref(params), ctypes.c_void_p(stream), ctypes.byref(out)),
            "dsnu_plan_create")
+    return out.value
+
+
+def dsnu_plan_create_multiplier(params: dsnu_params, mult: dsnu_multiplier, stream: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(load().dsnu_plan_create_multiplier(ctypes.byref(params), ctypes.byref(mult) if mult is not None
+                                              else None, ctypes.c_void_p(stream), ctypes.byref(out)),
+           "dsnu_plan_create_multiplier")
     return out.value
 
 

@@ -13,8 +13,8 @@ namespace dsnu {
 
 // Device tables of a plan.  Real-valued tables are in the plan's working
 // precision (float for DSNU_MIXED, double for DSNU_FP64); node_D is FP64.
-// The standard solver uses stw_x, stw_y, m_wx2 ((q_x dk_x)^2, q_x <= nx/2)
-// and status only.
+// The standard solver uses stw_x, stw_y, m_wx2 ((q_x dk_x)^2, q_x <= nx/2),
+// m_kx and status only.
 struct PlanTables {
   void* stw_x;    // cpx, FFT stage twiddles of length nx (fft_stage_tw_elems)
   void* twm_lo_x; // cpx, e^{-2 pi i n/Mx}, n < Lx = min(64, nx)
@@ -27,6 +27,7 @@ struct PlanTables {
   void* m_wx2;    // real, nx + 1  (q_x dk_x)^2
   void* m_gx;     // real, nx + 1  1 - exp(-(q_x dk_x)^2/sigma^2)
   void* m_gy;     // real, n_gy    1 - exp(-(a dk_y)^2/sigma^2), a < n_gy
+  void* m_kx;     // real, k_x per column for the sin 2theta term (0 at the Nyquist column); generic only
   int2* node_q0;  // n_nodes
   void* node_w;   // real, n_nodes * 2w (x weights then y weights)
   double* node_D; // n_nodes
@@ -73,6 +74,9 @@ struct PlanGeom {
   int spread_tile;         // its tile edge (cells)
   int precision, sharp;
   int standard;  // 1: the standard periodic FFT solver (kappa = 1, p = 0; standard.cuh)
+  // multiplier |k|^alpha (a0 + ac cos 2theta + as sin 2theta) when m_generic (else -k_x^2/|k|^2)
+  int m_generic, m_alpha;
+  double m_a0, m_ac, m_as;
   double beta, sigma, cut_radius;
   double scale;  // 1/(Mx My) (split solver) or 1/(nx ny) (standard solver)
 };

@@ -89,14 +89,35 @@ struct MultTabs {
   int half_my;        // N_y (= M_y / 2)
   int sharp;          // 1: p = indicator of |k| <= P
   R cut2;             // P^2
+  // another multiplier |k|^alpha (a0 + ac cos 2theta + as sin 2theta) when
+  // `generic` (the DS one, -k_x^2/|k|^2, otherwise)
+  int generic, alpha;
+  R a0, ac, as2;      // as2 = 2 as
+  R dky;              // dk_y
+  const R* kx;        // k_x of column q_x for the sin 2theta term (0 at the Nyquist column)
 };
+
+// The angular and radial factor of the generic multiplier at (k_x, qbar_y):
+// |k|^alpha (a0 + (ac (k_x^2 - k_y^2) + 2 as k_x k_y)/|k|^2), 0 at k = 0.
+// qs is the signed row index for the sin 2theta term, 0 at the Nyquist row:
+// there the aliases +K and -K are averaged (as the real part of a
+// full-spectrum evaluation does), which removes that odd term.
+template <typename R>
+__device__ __forceinline__ R mult_generic(const MultTabs<R>& mt, R wx2, R wy2, R kx, int qs, R s) {
+  if (s == R(0)) return R(0);
+  const R ang = mt.a0 + fdiv(mt.ac * (wx2 - wy2) + mt.as2 * kx * (R(qs) * mt.dky), s);
+  R rad = R(1);
+  if (mt.alpha == 1) rad = sqrt(s);
+  else if (mt.alpha == -1) rad = R(1) / sqrt(s);
+  return rad * ang;
+}
 
 // m1 = -(k_x^2/|k|^2) (1 - p(k)), m1(0) = 0, at column q_x and natural row
 // frequency q (signed qbar = q or q - M_y).  With the Gaussian partition
 // 1 - p = 1 - e^{-kx^2/s^2} e^{-ky^2/s^2} = gx + gy (1 - gx), a sum of
 // non-negative terms (no cancellation near k = 0).
 template <typename R>
-__device__ __forceinline__ R mult_high(const MultTabs<R>& mt, R wx2, R gx, int q) {
+__device__ __forceinline__ R mult_high(const MultTabs<R>& mt, R wx2, R kx, R gx, int q) {
   const int a = (q < mt.half_my) ? q : 2 * mt.half_my - q;
   const R wy2 = R(a * a) * mt.dky2;
   const R s = wx2 + wy2;
@@ -114,6 +135,9 @@ __device__ __forceinline__ R mult_high(const MultTabs<R>& mt, R wx2, R gx, int q
     const R gy = (a < mt.n_gy) ? -expm1_r(-wy2 * mt.inv_sigma2) : R(1);
     part = gx + gy * (R(1) - gx);
   }
+  if (mt.generic)
+    return mult_generic(mt, wx2, wy2, kx, (q < mt.half_my) ? q : (q == mt.half_my ? 0 : q - 2 * mt.half_my), s) *
+           part;
   return -fdiv(wx2, s) * part;
 }
 
@@ -284,6 +308,7 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
     const bool valid = col < ncols;
     const R wx2 = valid ? mt.wx2[col] : R(0);
     const R gx = valid ? mt.gx[col] : R(0);
+    const R kxc = (valid && mt.generic) ? mt.kx[col] : R(0);
     cpx<R> e[16], o[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -298,8 +323,8 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int q = 2 * (t + G * m);
-      e[m] = e[m] * (valid ? mult_high(mt, wx2, gx, q) : R(0));
-      o[m] = o[m] * (valid ? mult_high(mt, wx2, gx, q + 1) : R(0));
+      e[m] = e[m] * (valid ? mult_high(mt, wx2, kxc, gx, q) : R(0));
+      o[m] = o[m] * (valid ? mult_high(mt, wx2, kxc, gx, q + 1) : R(0));
     }
     block_fft2_regs<R, LOG2N>(e, o, buf_e, buf_o, t, stw, cj == 0);
     if (valid) {
@@ -343,6 +368,7 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
     const bool valid = col < ncols;
     const R wx2 = valid ? mt.wx2[col] : R(0);
     const R gx = valid ? mt.gx[col] : R(0);
+    const R kxc = (valid && mt.generic) ? mt.kx[col] : R(0);
 #pragma unroll 1
     for (int par = 0; par < 2; ++par) {
       cpx<R> v[16];
@@ -361,7 +387,7 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int q = 2 * (t + G * m) + par;
-        v[m] = v[m] * (valid ? mult_high(mt, wx2, gx, q) : R(0));
+        v[m] = v[m] * (valid ? mult_high(mt, wx2, kxc, gx, q) : R(0));
       }
       block_fft_regs<R, LOG2N>(v, buf, t, stw, cj == 0);
       if (par == 0) {

@@ -1,6 +1,8 @@
 // pipeline.cuh -- launch sequence of one solve (included once per precision).
 #pragma once
 
+#include <cmath>
+
 #include "internal.h"
 #include "kernels.cuh"
 #include "standard.cuh"
@@ -129,7 +131,16 @@ dsnu_status run_standard(const PlanGeom& g, const PlanTables& t, const WsLayout&
                          cudaStream_t st, int cj, cudaEvent_t* ev) {
   const cpx<R>* sx = static_cast<const cpx<R>*>(t.stw_x);
   const cpx<R>* sy = static_cast<const cpx<R>*>(t.stw_y);
-  const R* wx2 = static_cast<const R*>(t.m_wx2);
+  MultTabs<R> mt{};
+  mt.wx2 = static_cast<const R*>(t.m_wx2);
+  mt.dky2 = R(g.dky2);
+  mt.dky = R(std::sqrt(g.dky2));
+  mt.generic = g.m_generic;
+  mt.alpha = g.m_alpha;
+  mt.a0 = R(g.m_a0);
+  mt.ac = R(g.m_ac);
+  mt.as2 = R(2.0 * g.m_as);
+  mt.kx = static_cast<const R*>(t.m_kx);
   const long nm = mem.count;
   const int ldq = L.ldqA;
 #define DSNU_SROWF(L2)                                                                         \
@@ -139,8 +150,8 @@ dsnu_status run_standard(const PlanGeom& g, const PlanTables& t, const WsLayout&
 #define DSNU_SCOL(L2)                                                                          \
   k_std_col<R, L2><<<persistent_grid(nm * ((ldq + GeoStd<R, L2>::PER - 1) / GeoStd<R, L2>::PER), \
                                      g.cap_col),                                                \
-                     GeoStd<R, L2>::T, GeoStd<R, L2>::smem, st>>>(mem, L.off_A, ldq, ldq, sy, wx2, \
-                                                                  R(g.dky2), R(g.scale), cj)
+                     GeoStd<R, L2>::T, GeoStd<R, L2>::smem, st>>>(mem, L.off_A, ldq, ldq, sy, mt,  \
+                                                                  R(g.scale), cj)
 #define DSNU_SROWI(L2)                                                                         \
   k_std_row_inv<R, L2><<<persistent_grid(nm * ((g.ny / 2 + GeoStd<R, L2>::PER - 1) /            \
                                                GeoStd<R, L2>::PER), g.cap_rowi),               \
@@ -185,7 +196,8 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
   const MultTabs<R> mt{static_cast<const R*>(t.m_wx2), static_cast<const R*>(t.m_gx),
                        g.n_gy, R(1.0 / (g.sigma * g.sigma)),
                        R(-g.dky2 / (g.sigma * g.sigma) * 1.4426950408889634), R(g.dky2), g.ny, g.sharp,
-                       R(g.cut_radius * g.cut_radius)};
+                       R(g.cut_radius * g.cut_radius), g.m_generic, g.m_alpha, R(g.m_a0), R(g.m_ac),
+                       R(2.0 * g.m_as), R(std::sqrt(g.dky2)), static_cast<const R*>(t.m_kx)};
   const R* dcy = static_cast<const R*>(t.decon_y);
   const R* wts = static_cast<const R*>(t.node_w);
   const int ldqA = L.ldqA, ldqB = L.ldqB;

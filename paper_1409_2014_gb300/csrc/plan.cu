@@ -197,7 +197,7 @@ template <typename R>
 struct HostTables {
   // complex tables interleaved (re, im)
   std::vector<R> stw_x, twm_lo_x, twm_hi_x, decon_x, stw_y, twm_lo_y, twm_hi_y, decon_y;
-  std::vector<R> m_wx2, m_gx, m_gy;
+  std::vector<R> m_wx2, m_gx, m_gy, m_kx;
   std::vector<int2> node_q0;
   std::vector<R> node_w;
   std::vector<double> node_D;
@@ -451,7 +451,12 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
       const double c = std::cos(th), s = std::sin(th);
       kx[i * p.n_theta + j] = r * c;
       ky[i * p.n_theta + j] = r * s;
-      D[i * p.n_theta + j] = -(rw[i] * (2.0 * M_PI / p.n_theta) * c * c * pr) / (4.0 * M_PI * M_PI);
+      if (g.m_generic)  // r^alpha (a0 + ac cos 2theta + as sin 2theta) in place of -cos^2 theta
+        D[i * p.n_theta + j] = (rw[i] * std::pow(r, double(g.m_alpha)) *
+                                (g.m_a0 + g.m_ac * (c * c - s * s) + g.m_as * 2.0 * s * c) *
+                                (2.0 * M_PI / p.n_theta) * pr) / (4.0 * M_PI * M_PI);
+      else
+        D[i * p.n_theta + j] = -(rw[i] * (2.0 * M_PI / p.n_theta) * c * c * pr) / (4.0 * M_PI * M_PI);
     }
   }
 
@@ -477,10 +482,12 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   // working precision ((a dk_y)^2 itself is formed in the kernel)
   T.m_wx2.resize(nx + 1);
   T.m_gx.resize(nx + 1);
+  T.m_kx.resize(nx + 1);
   for (int q = 0; q <= nx; ++q) {
     const double a = q * dkx;
     T.m_wx2[q] = R(a * a);
     T.m_gx[q] = R(-std::expm1(-(a * a) / (sigma * sigma)));
+    T.m_kx[q] = R(q < nx ? a : 0.0);  // Nyquist column: +-K averaged, the sin 2theta term vanishes
   }
   g.dky2 = dky * dky;
   T.m_gy.clear();
@@ -524,7 +531,7 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   const size_t o_dx = b.add(T.decon_x);
   const size_t o_sty = b.add(T.stw_y), o_tly = b.add(T.twm_lo_y), o_thy = b.add(T.twm_hi_y);
   const size_t o_dy = b.add(T.decon_y);
-  const size_t o_wx2 = b.add(T.m_wx2), o_gx = b.add(T.m_gx), o_gy = b.add(T.m_gy);
+  const size_t o_wx2 = b.add(T.m_wx2), o_gx = b.add(T.m_gx), o_gy = b.add(T.m_gy), o_kx = b.add(T.m_kx);
   const size_t o_q0 = b.add(T.node_q0), o_w = b.add(T.node_w), o_D = b.add(T.node_D);
   const int zero = 0;
   const size_t o_st = b.add(&zero, sizeof(int));
@@ -541,7 +548,7 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   PlanTables& t = P->tab;
   t.stw_x = d + o_stx; t.twm_lo_x = d + o_tlx; t.twm_hi_x = d + o_thx; t.decon_x = d + o_dx;
   t.stw_y = d + o_sty; t.twm_lo_y = d + o_tly; t.twm_hi_y = d + o_thy; t.decon_y = d + o_dy;
-  t.m_wx2 = d + o_wx2; t.m_gx = d + o_gx; t.m_gy = d + o_gy;
+  t.m_wx2 = d + o_wx2; t.m_gx = d + o_gx; t.m_gy = d + o_gy; t.m_kx = d + o_kx;
   t.node_q0 = reinterpret_cast<int2*>(d + o_q0);
   t.node_w = d + o_w;
   t.node_D = reinterpret_cast<double*>(d + o_D);
@@ -563,11 +570,14 @@ static dsnu_status build_tables_standard(dsnu_plan_s* P, cudaStream_t st) {
   fft_stage_twiddles(g.log2ny, tmp);
   const std::vector<R> stw_y = cast<R>(tmp);
   const double dkx = M_PI / p.lx, dky = M_PI / p.ly;
-  std::vector<R> wx2(g.nx / 2 + 1);
-  for (int q = 0; q <= g.nx / 2; ++q) wx2[q] = R((q * dkx) * (q * dkx));
+  std::vector<R> wx2(g.nx / 2 + 1), kx(g.nx / 2 + 1);
+  for (int q = 0; q <= g.nx / 2; ++q) {
+    wx2[q] = R((q * dkx) * (q * dkx));
+    kx[q] = R(q < g.nx / 2 ? q * dkx : 0.0);  // Nyquist column: +-K averaged (no sin 2theta term)
+  }
   g.dky2 = dky * dky;
   Builder b;
-  const size_t o_stx = b.add(stw_x), o_sty = b.add(stw_y), o_wx2 = b.add(wx2);
+  const size_t o_stx = b.add(stw_x), o_sty = b.add(stw_y), o_wx2 = b.add(wx2), o_kx = b.add(kx);
   const int zero = 0;
   const size_t o_st = b.add(&zero, sizeof(int));
   void* dev = nullptr;
@@ -584,6 +594,7 @@ static dsnu_status build_tables_standard(dsnu_plan_s* P, cudaStream_t st) {
   t.stw_x = d + o_stx;
   t.stw_y = d + o_sty;
   t.m_wx2 = d + o_wx2;
+  t.m_kx = d + o_kx;
   t.status = reinterpret_cast<int*>(d + o_st);
   P->table_block = dev;
   P->table_bytes = b.bytes.size();
@@ -627,7 +638,17 @@ extern "C" {
 const char* dsnu_last_error(void) { return g_last_error.c_str(); }
 
 dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan* out) {
+  return dsnu_plan_create_multiplier(params, nullptr, stream, out);
+}
+
+dsnu_status dsnu_plan_create_multiplier(const dsnu_params* params, const dsnu_multiplier* mult, void* stream,
+                                        dsnu_plan* out) {
   if (!params || !out) return fail(DSNU_EINVAL, "NULL params or out");
+  if (mult) {
+    if (mult->alpha < -1 || mult->alpha > 1) return fail(DSNU_EINVAL, "multiplier alpha must be -1, 0 or 1");
+    if (!std::isfinite(mult->a0) || !std::isfinite(mult->a_cos) || !std::isfinite(mult->a_sin))
+      return fail(DSNU_EINVAL, "multiplier coefficients must be finite");
+  }
   dsnu_params p = *params;
   if (!is_pow2(p.nx) || !is_pow2(p.ny) || p.nx < 16 || p.ny < 16 || p.nx > 4096 || p.ny > 4096)
     return fail(DSNU_EINVAL, "nx, ny must be powers of two in [16, 4096]");
@@ -669,6 +690,13 @@ dsnu_status dsnu_plan_create(const dsnu_params* params, void* stream, dsnu_plan*
   g.nx = p.nx;
   g.ny = p.ny;
   g.standard = standard ? 1 : 0;
+  if (mult) {
+    g.m_generic = 1;
+    g.m_alpha = mult->alpha;
+    g.m_a0 = mult->a0;
+    g.m_ac = mult->a_cos;
+    g.m_as = mult->a_sin;
+  }
   g.mx = p.pad_factor * p.nx;
   g.my = p.pad_factor * p.ny;
   g.log2nx = ilog2(p.nx);

@@ -10,7 +10,8 @@
 //                   half spectra q in [0, N_x/2] separated by Hermitian
 //                   symmetry and stored row-tiled (both rows in one store);
 //   k_std_col     : per half-spectrum column: DFT along y, times m / (N_x N_y),
-//                   inverse DFT along y, in place;
+//                   inverse DFT along y, in place (m: the DS multiplier or
+//                   the generic family of MultTabs);
 //   k_std_row_inv : two rows per transform again (W = Y_a + i Y_b, each
 //                   extended to q > N_x/2 by conjugate symmetry); the real and
 //                   imaginary parts of the inverse are the two rows of Phi.
@@ -86,7 +87,7 @@ k_std_row_fwd(Members mem, size_t offH, int ldq, int ny, const cpx<R>* __restric
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(GeoStd<R, LOG2N>::T, min_blocks<R>(2))
 k_std_col(Members mem, size_t offH, int ldq, int ncols, const cpx<R>* __restrict__ stw_g,
-          const R* __restrict__ wx2, R dky2, R scale, int cj) {
+          MultTabs<R> mt, R scale, int cj) {
   using GG = GeoStd<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, PER = GG::PER;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -102,7 +103,8 @@ k_std_col(Members mem, size_t offH, int ldq, int ncols, const cpx<R>* __restrict
     cpx<R>* __restrict__ H = ws_ptr<cpx<R>>(member_at(mem, mi), offH);
     const int col = item * PER + cl;
     const bool valid = col < ncols;
-    const R kx2 = valid ? wx2[col] : R(0);
+    const R kx2 = valid ? mt.wx2[col] : R(0);
+    const R kxc = (valid && mt.generic) ? mt.kx[col] : R(0);
     cpx<R> v[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = valid ? H[Tile<R>::at(t + G * m, col, ldq)] : mk<R>(R(0), R(0));
@@ -111,8 +113,13 @@ k_std_col(Members mem, size_t offH, int ldq, int ncols, const cpx<R>* __restrict
     for (int m = 0; m < 16; ++m) {
       const int q = t + G * m;  // natural order after the transform
       const int a = (q <= N / 2) ? q : N - q;
-      const R s = kx2 + R(a * a) * dky2;
-      const R mlt = (s == R(0)) ? R(0) : -fdiv(kx2, s) * scale;
+      const R wy2 = R(a * a) * mt.dky2;
+      const R s = kx2 + wy2;
+      R mlt;
+      if (mt.generic)  // signed qbar for the sin 2theta term, 0 at the Nyquist row
+        mlt = mult_generic(mt, kx2, wy2, kxc, (q < N / 2) ? q : (q == N / 2 ? 0 : q - N), s) * scale;
+      else
+        mlt = (s == R(0)) ? R(0) : -fdiv(kx2, s) * scale;
       v[m] = v[m] * mlt;
     }
     block_fft_regs<R, LOG2N>(v, buf, t, stw, cj == 0);

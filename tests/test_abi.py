@@ -53,7 +53,7 @@ def test_struct_layout_matches_header(tmp_path):
         pytest.skip("no C compiler")
     checks = []
     for struct, cls in (("dsnu_params", _abi.dsnu_params), ("dsnu_plan_info", _abi.dsnu_plan_info),
-                        ("dsnu_ds_params", _abi.dsnu_ds_params)):
+                        ("dsnu_ds_params", _abi.dsnu_ds_params), ("dsnu_multiplier", _abi.dsnu_multiplier)):
         checks.append(f'printf("{struct} sizeof %zu\\n", sizeof({struct}));')
         for name, _ in cls._fields_:
             checks.append(f'printf("{struct} {name} %zu\\n", offsetof({struct}, {name}));')
@@ -65,7 +65,7 @@ def test_struct_layout_matches_header(tmp_path):
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
     got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line.strip()}
     for struct, cls in (("dsnu_params", _abi.dsnu_params), ("dsnu_plan_info", _abi.dsnu_plan_info),
-                        ("dsnu_ds_params", _abi.dsnu_ds_params)):
+                        ("dsnu_ds_params", _abi.dsnu_ds_params), ("dsnu_multiplier", _abi.dsnu_multiplier)):
         assert got[(struct, "sizeof")] == ctypes.sizeof(cls), struct
         for name, _ in cls._fields_:
             assert got[(struct, name)] == getattr(cls, name).offset, (struct, name)
@@ -134,6 +134,14 @@ def test_standard_solver_needs_pad_factor_one(lib):
         with pytest.raises(_abi.DsnuError) as ei:
             _abi.dsnu_plan_create(q, 0)
         assert ei.value.status == _abi.DSNU_EINVAL
+
+
+@pytest.mark.parametrize("alpha,a0", [(2, 1.0), (-2, 1.0), (0, float("inf"))])
+def test_bad_multiplier_is_rejected(lib, alpha, a0):
+    m = _abi.dsnu_multiplier(alpha=alpha, reserved=0, a0=a0, a_cos=0.0, a_sin=0.0)
+    with pytest.raises(_abi.DsnuError) as ei:
+        _abi.dsnu_plan_create_multiplier(_params(), m, 0)
+    assert ei.value.status == _abi.DSNU_EINVAL
 
 
 def test_null_plan_calls(lib):
