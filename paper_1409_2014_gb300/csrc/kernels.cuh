@@ -116,7 +116,7 @@ __device__ __forceinline__ R mult_generic(const MultTabs<R>& mt, R wx2, R wy2, R
 // frequency q (signed qbar = q or q - M_y).  With the Gaussian partition
 // 1 - p = 1 - e^{-kx^2/s^2} e^{-ky^2/s^2} = gx + gy (1 - gx), a sum of
 // non-negative terms (no cancellation near k = 0).
-template <typename R>
+template <bool GEN, typename R>
 __device__ __forceinline__ R mult_high(const MultTabs<R>& mt, R wx2, R kx, R gx, int q) {
   const int a = (q < mt.half_my) ? q : 2 * mt.half_my - q;
   const R wy2 = R(a * a) * mt.dky2;
@@ -135,10 +135,11 @@ __device__ __forceinline__ R mult_high(const MultTabs<R>& mt, R wx2, R kx, R gx,
     const R gy = (a < mt.n_gy) ? -expm1_r(-wy2 * mt.inv_sigma2) : R(1);
     part = gx + gy * (R(1) - gx);
   }
-  if (mt.generic)
+  if constexpr (GEN)
     return mult_generic(mt, wx2, wy2, kx, (q < mt.half_my) ? q : (q == mt.half_my ? 0 : q - 2 * mt.half_my), s) *
            part;
-  return -fdiv(wx2, s) * part;
+  else
+    return -fdiv(wx2, s) * part;
 }
 
 // Workspace offsets (bytes) of one member's buffers, and member access.
@@ -193,6 +194,10 @@ struct Geo {
   static constexpr size_t smem_row_fwd = size_t(STWP + 2 * RB_F * RS) * sizeof(cpx<R>);
   static constexpr size_t smem_row_inv = size_t(STWP + 2 * RB_I * RS) * sizeof(cpx<R>);
   static constexpr size_t smem_col = size_t(STWP + 2 * CC * FB) * sizeof(cpx<R>);  // two chains
+  // FP32 column pass of I1 with the DS multiplier: two shared tables on top,
+  // e^{-2 pi i n/M} (n < N) and {(a dk_y)^2, e^{-(a dk_y)^2/sigma^2}} (a <= N)
+  static constexpr bool COL_TAB = sizeof(R) == 4;
+  static constexpr size_t smem_col_main = smem_col + (COL_TAB ? size_t(N) * 8 + size_t(N + 1) * 8 : 0);
   static constexpr size_t smem_band_fwd = size_t(STWP + CC * FB) * sizeof(cpx<R>);
   static_assert(LOG2N >= 4 && LOG2N <= 12, "grid size 16..4096");
 };
@@ -285,11 +290,17 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
 // padded column DFT) go forward together, are multiplied by m1 and come back
 // together; their sum is the column of I1's inverse.  All loads of a column
 // precede the first barrier, so the in-place update is safe.
-template <typename R, int LOG2N>
+template <typename R, int LOG2N, bool GEN>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COLMAIN_MINB))
 k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs<R> mt, int cj) {
   using GG = Geo<R, LOG2N>;
-  constexpr int G = GG::G, CC = GG::CC, FB = GG::FB;
+  constexpr int N = GG::N, G = GG::G, CC = GG::CC, FB = GG::FB;
+  // FP32 with the DS multiplier: the e^{-2 pi i n/M} factors of the odd chain
+  // and the row-dependent parts of m1 ((a dk_y)^2 and e^{-(a dk_y)^2/sigma^2},
+  // a = |qbar_y|, the same for every column) come from shared tables filled
+  // once per CTA with the arithmetic of twm() and mult_high(), so the results
+  // are unchanged
+  constexpr bool TAB = GG::COL_TAB && !GEN;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* sm = stw + GG::STWP;
@@ -299,6 +310,16 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
   const R isg = cj ? R(-1) : R(1);
   cpx<R>* buf_e = sm + (2 * cl) * FB;
   cpx<R>* buf_o = buf_e + FB;
+  cpx<R>* wtab = sm + 2 * CC * FB;                       // N entries (TAB only)
+  float2* mtab = reinterpret_cast<float2*>(wtab + N);    // N + 1 entries (TAB only)
+  if constexpr (TAB) {
+    for (int i = tid; i < N; i += GG::T_C) wtab[i] = twm(ay, i);
+    for (int i = tid; i <= N; i += GG::T_C) {
+      const R a2 = R(i * i);
+      mtab[i] = make_float2(a2 * mt.dky2, exp2f(a2 * mt.neg_dky2_s2_log2e));
+    }
+    __syncthreads();
+  }
   const int items = (ncols + CC - 1) / CC;
 #pragma unroll 1
   for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
@@ -308,13 +329,15 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
     const bool valid = col < ncols;
     const R wx2 = valid ? mt.wx2[col] : R(0);
     const R gx = valid ? mt.gx[col] : R(0);
-    const R kxc = (valid && mt.generic) ? mt.kx[col] : R(0);
+    const R kxc = (GEN && valid) ? mt.kx[col] : R(0);
     cpx<R> e[16], o[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int n = t + G * m;
       const cpx<R> x = valid ? A[Tile<R>::at(n, col, ldqA)] : mk<R>(R(0), R(0));
-      cpx<R> w = twm(ay, n);
+      cpx<R> w;
+      if constexpr (TAB) w = wtab[n];
+      else w = twm(ay, n);
       w.y *= isg;
       e[m] = x;
       o[m] = cmul(x, w);
@@ -323,15 +346,32 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int q = 2 * (t + G * m);
-      e[m] = e[m] * (valid ? mult_high(mt, wx2, kxc, gx, q) : R(0));
-      o[m] = o[m] * (valid ? mult_high(mt, wx2, kxc, gx, q + 1) : R(0));
+      if constexpr (TAB) {
+        // m1 at rows q and q + 1 (a = |qbar|), branch-free; equal to mult_high
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int qq = q + h;
+          const int a = (qq < N) ? qq : 2 * N - qq;
+          const float2 tv = mtab[a];
+          const R s = wx2 + tv.x;
+          const R part = mt.sharp ? ((s > mt.cut2) ? R(1) : R(0)) : (R(1) - (R(1) - gx) * tv.y);
+          const R mv = (s == R(0) || !valid) ? R(0) : -fdiv(wx2, (s == R(0)) ? R(1) : s) * part;
+          if (h == 0) e[m] = e[m] * mv;
+          else o[m] = o[m] * mv;
+        }
+      } else {
+        e[m] = e[m] * (valid ? mult_high<GEN>(mt, wx2, kxc, gx, q) : R(0));
+        o[m] = o[m] * (valid ? mult_high<GEN>(mt, wx2, kxc, gx, q + 1) : R(0));
+      }
     }
     block_fft2_regs<R, LOG2N>(e, o, buf_e, buf_o, t, stw, cj == 0);
     if (valid) {
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int n = t + G * m;
-        const cpx<R> w = twm(ay, n);
+        cpx<R> w;
+        if constexpr (TAB) w = wtab[n];
+        else w = twm(ay, n);
         A[Tile<R>::at(n, col, ldqA)] = cj ? e[m] + cmul(o[m], w) : e[m] + cmulc(o[m], w);
       }
     }
@@ -345,7 +385,7 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
 // variant).  The odd
 // chain's loads of a column precede its first barrier, so the in-place update
 // is safe.
-template <typename R, int LOG2N>
+template <typename R, int LOG2N, bool GEN>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
 k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs<R> mt, int cj) {
   using GG = Geo<R, LOG2N>;
@@ -368,7 +408,7 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
     const bool valid = col < ncols;
     const R wx2 = valid ? mt.wx2[col] : R(0);
     const R gx = valid ? mt.gx[col] : R(0);
-    const R kxc = (valid && mt.generic) ? mt.kx[col] : R(0);
+    const R kxc = (GEN && valid) ? mt.kx[col] : R(0);
 #pragma unroll 1
     for (int par = 0; par < 2; ++par) {
       cpx<R> v[16];
@@ -387,7 +427,7 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int q = 2 * (t + G * m) + par;
-        v[m] = v[m] * (valid ? mult_high(mt, wx2, kxc, gx, q) : R(0));
+        v[m] = v[m] * (valid ? mult_high<GEN>(mt, wx2, kxc, gx, q) : R(0));
       }
       block_fft_regs<R, LOG2N>(v, buf, t, stw, cj == 0);
       if (par == 0) {
