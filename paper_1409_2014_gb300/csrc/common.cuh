@@ -379,53 +379,16 @@ __device__ __forceinline__ void copy_to_smem(T* __restrict__ dst, const T* __res
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
-// ---------------------------------------------------------------------------
-// FP64 <-> FP32 conversions in integer arithmetic (IEEE-754 binary64/binary32
-// bit layouts).  On GB300 the hardware conversion instructions issue on the
-// FP64 pipe, which runs at a small fraction of the FP32 rate; these run on the
-// integer pipes.  f64 -> f32 rounds to nearest even for results in the normal
-// float range, flushes results below 2^-126 to a signed zero and overflows to
-// infinity; f32 -> f64 is exact for normal floats, flushes float subnormals to
-// zero and maps infinities/NaNs to infinities/NaNs.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float f64_to_f32_bits(double d) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
-  const unsigned int hi = static_cast<unsigned int>(b >> 32);
-  const unsigned int lo = static_cast<unsigned int>(b);
-  const unsigned int sign = hi & 0x80000000u;
-  const int e = static_cast<int>((hi >> 20) & 0x7FFu) - 1023 + 127;
-  const unsigned int m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);  // top 23 mantissa bits
-  const unsigned int rest = lo & 0x1FFFFFFFu;                   // dropped 29 bits
-  unsigned int r = (static_cast<unsigned int>(e) << 23) + m;
-  r += (rest > 0x10000000u) || (rest == 0x10000000u && (m & 1u));  // nearest, ties to even
-  r = (e <= 0) ? 0u : r;
-  r = (e >= 255) ? 0x7F800000u : r;
-  return __uint_as_float(sign | r);
-}
-
-__device__ __forceinline__ double f32_to_f64_bits(float f) {
-  const unsigned int u = __float_as_uint(f);
-  const unsigned int sign = u & 0x80000000u;
-  const unsigned int e = (u >> 23) & 0xFFu;
-  const unsigned int m = u & 0x7FFFFFu;
-  const unsigned int e64 = (e == 255u) ? 2047u : (e + (1023u - 127u));
-  unsigned int hi = sign | (e64 << 20) | (m >> 3);
-  unsigned int lo = m << 29;
-  hi = (e == 0u) ? sign : hi;
-  lo = (e == 0u) ? 0u : lo;
-  return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
-}
-
 // Conversions used at the FP64 boundary of the pipeline (identity for double).
+// (round to nearest; FP32 -> FP64 is exact)
 template <typename R>
 __device__ __forceinline__ R from_f64(double d) {
-  if constexpr (sizeof(R) == 4) return f64_to_f32_bits(d);
+  if constexpr (sizeof(R) == 4) return __double2float_rn(d);
   else return d;
 }
 template <typename R>
 __device__ __forceinline__ double to_f64(R v) {
-  if constexpr (sizeof(R) == 4) return f32_to_f64_bits(v);
-  else return v;
+  return static_cast<double>(v);
 }
 
 // expm1 in the working precision (library function).

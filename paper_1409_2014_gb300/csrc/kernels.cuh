@@ -49,10 +49,10 @@
 #define DSNU_COL_MINB 2
 #endif
 #ifndef DSNU_ROWF_RB32
-#define DSNU_ROWF_RB32 1
+#define DSNU_ROWF_RB32 2
 #endif
 #ifndef DSNU_ROWI_RB32
-#define DSNU_ROWI_RB32 1
+#define DSNU_ROWI_RB32 2
 #endif
 #ifndef DSNU_COL_PAIRED
 #define DSNU_COL_PAIRED 1
@@ -191,8 +191,16 @@ struct Geo {
   static constexpr int T_C = CC * G;
   static constexpr int STW = fft_stage_tw_elems(LOG2N) > 0 ? fft_stage_tw_elems(LOG2N) : 1;
   static constexpr int STWP = (STW + 1) & ~1;  // keep the buffers 16-byte aligned
-  static constexpr size_t smem_row_fwd = size_t(STWP + 2 * RB_F * RS) * sizeof(cpx<R>);
-  static constexpr size_t smem_row_inv = size_t(STWP + 2 * RB_I * RS) * sizeof(cpx<R>);
+  // FP32 row passes keep e^{-2 pi i n/M} (n < N) in a shared table after the buffers
+  static constexpr bool ROW_TAB = sizeof(R) == 4;
+  static constexpr size_t smem_row_fwd = size_t(STWP + 2 * RB_F * RS + (ROW_TAB ? N : 0)) * sizeof(cpx<R>);
+  static constexpr size_t smem_row_inv = size_t(STWP + 2 * RB_I * RS + (ROW_TAB ? N : 0)) * sizeof(cpx<R>);
+  // two rows of 512 threads: their threads interleave lane by lane, so that
+  // the two rows' elements of a 32-byte row tile are touched by adjacent lanes
+  static constexpr bool ILV_F = (RB_F == 2);
+  static constexpr bool ILV_I = (RB_I == 2);
+  static constexpr int MINB_F = (T_RF >= 512) ? 1 : DSNU_ROW_MINB;
+  static constexpr int MINB_I = (T_RI >= 512) ? 1 : DSNU_ROW_MINB;
   static constexpr size_t smem_col = size_t(STWP + 2 * CC * FB) * sizeof(cpx<R>);  // two chains
   // FP32 column pass of I1 with the DS multiplier: two shared tables on top,
   // e^{-2 pi i n/M} (n < N) and {(a dk_y)^2, e^{-(a dk_y)^2/sigma^2}} (a <= N)
@@ -212,7 +220,7 @@ struct Geo {
 // interleaved length-N transforms of z and z w_M^n), then the two real-signal
 // spectra are separated at every q in [0, N].
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RF, min_blocks<R>(DSNU_ROW_MINB))
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RF, min_blocks<R>(Geo<R, LOG2N>::MINB_F))
 k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
           const R* __restrict__ decon_y, int cj) {
   using GG = Geo<R, LOG2N>;
@@ -220,9 +228,14 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* sm = stw + GG::STWP;
+  cpx<R>* wtab = sm + 2 * RB * RS;  // e^{-2 pi i n/M}, n < N (FP32)
   copy_to_smem(stw, ax.stw, GG::STW);
+  if constexpr (GG::ROW_TAB)
+    for (int i = threadIdx.x; i < N; i += T) wtab[i] = twm(ax, i);
+  __syncthreads();
   const int tid = threadIdx.x;
-  const int rr = tid / G, t = tid - rr * G;
+  const int rr = GG::ILV_F ? (tid & 1) : tid / G;
+  const int t = GG::ILV_F ? (tid >> 1) : tid - rr * G;
   const R isg = cj ? R(-1) : R(1);
   cpx<R>* buf_e = sm + (2 * rr) * RS;
   cpx<R>* buf_o = buf_e + RS;
@@ -244,7 +257,9 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
       const int n = t + G * m;
       const R x = valid ? from_f64<R>(rho[size_t(row) * N + n]) : R(0);
       const cpx<R> z = mk<R>(x, isg * (x * ax.decon[n] * dy));
-      cpx<R> w = twm(ax, n);
+      cpx<R> w;
+      if constexpr (GG::ROW_TAB) w = wtab[n];
+      else w = twm(ax, n);
       w.y *= isg;
       e[m] = z;
       o[m] = cmul(z, w);
@@ -716,7 +731,7 @@ k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs
 // with W(q) = Y(q) + i S(q) for q <= N and W(M - q) = conj Y(q) + i conj S(q).
 // Both transforms run together; j < N/2 gives the grid points n < N.
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(DSNU_ROW_MINB))
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(Geo<R, LOG2N>::MINB_I))
 k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
           const R* __restrict__ decon_y, R scale, int cj) {
   using GG = Geo<R, LOG2N>;
@@ -724,9 +739,14 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* sm = stw + GG::STWP;
+  cpx<R>* wtab = sm + 2 * RB * RS;  // e^{-2 pi i q/M}, q < N (FP32)
   copy_to_smem(stw, ax.stw, GG::STW);
+  if constexpr (GG::ROW_TAB)
+    for (int i = threadIdx.x; i < N; i += GG::T_RI) wtab[i] = twm(ax, i);
+  __syncthreads();
   const int tid = threadIdx.x;
-  const int rr = tid / G, t = tid - rr * G;
+  const int rr = GG::ILV_I ? (tid & 1) : tid / G;
+  const int t = GG::ILV_I ? (tid >> 1) : tid - rr * G;
   const int si = cj ? -1 : 1;
   cpx<R>* buf_u = sm + (2 * rr) * RS;
   cpx<R>* buf_v = buf_u + RS;
@@ -781,7 +801,9 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
       const cpx<R> wlo = y[m] + mul_i(s[m], si);
       const cpx<R> whi = yh + mul_i(sh, si);
       a[m] = wlo + whi;
-      const cpx<R> w = twm(ax, q);  // e^{-2 pi i q/M}; the inverse uses its conjugate
+      cpx<R> w;  // e^{-2 pi i q/M}; the inverse uses its conjugate
+      if constexpr (GG::ROW_TAB) w = wtab[q];
+      else w = twm(ax, q);
       const cpx<R> d = wlo - whi;
       b[m] = cj ? cmul(d, w) : cmulc(d, w);
     }
