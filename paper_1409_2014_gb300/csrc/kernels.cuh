@@ -57,6 +57,9 @@
 #ifndef DSNU_COL_PAIRED
 #define DSNU_COL_PAIRED 1
 #endif
+#ifndef DSNU_TILE_LT32
+#define DSNU_TILE_LT32 2
+#endif
 #ifndef DSNU_COLMAIN_MINB
 #define DSNU_COLMAIN_MINB 1
 #endif
@@ -155,7 +158,7 @@ __device__ __forceinline__ T* ws_ptr(const Member& mb, size_t off) {
 // Row tiling of the intermediate spectra (see the file comment).
 template <typename R>
 struct Tile {
-  static constexpr int LT = (sizeof(R) == 4) ? 2 : 1;  // log2 rows per tile
+  static constexpr int LT = (sizeof(R) == 4) ? DSNU_TILE_LT32 : 1;  // log2 rows per tile
   static constexpr int TR = 1 << LT;
   __device__ __forceinline__ static size_t at(int iy, int q, int ldq) {
     return ((size_t(iy >> LT) * ldq + q) << LT) | size_t(iy & (TR - 1));
@@ -206,7 +209,6 @@ struct Geo {
   // e^{-2 pi i n/M} (n < N) and {(a dk_y)^2, e^{-(a dk_y)^2/sigma^2}} (a <= N)
   static constexpr bool COL_TAB = sizeof(R) == 4;
   static constexpr size_t smem_col_main = smem_col + (COL_TAB ? size_t(N) * 8 + size_t(N + 1) * 8 : 0);
-  static constexpr size_t smem_band_fwd = size_t(STWP + CC * FB) * sizeof(cpx<R>);
   static_assert(LOG2N >= 4 && LOG2N <= 12, "grid size 16..4096");
 };
 
@@ -464,6 +466,8 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
 #endif
 
 // ---------------------------------------------------------------------------
+// Band columns of the type-2 spectrum: per column of B, both output parities
+// of the padded column DFT in one paired transform; rows |qbar| <= Q kept.
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
 k_band_fwd(Members mem, WsOff off, int ldqB, int ncols, int ldq, int Q, AxisTabs<R> ay, int cj) {
@@ -476,7 +480,8 @@ k_band_fwd(Members mem, WsOff off, int ldqB, int ncols, int ldq, int Q, AxisTabs
   const int tid = threadIdx.x;
   const int cl = tid / G, t = tid - cl * G;
   const R isg = cj ? R(-1) : R(1);
-  cpx<R>* buf = sm + cl * FB;
+  cpx<R>* buf_e = sm + (2 * cl) * FB;
+  cpx<R>* buf_o = buf_e + FB;
   const int items = (ncols + CC - 1) / CC;
 #pragma unroll 1
   for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
@@ -486,28 +491,25 @@ k_band_fwd(Members mem, WsOff off, int ldqB, int ncols, int ldq, int Q, AxisTabs
     cpx<R>* __restrict__ Bband = ws_ptr<cpx<R>>(mb, off.Bband);
     const int col = item * CC + cl;
     const bool valid = col < ncols;
-#pragma unroll 1
-    for (int par = 0; par < 2; ++par) {
-      cpx<R> v[16];
+    cpx<R> e[16], o[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int n = t + G * m;
+      const cpx<R> x = valid ? B[Tile<R>::at(n, col, ldqB)] : mk<R>(R(0), R(0));
+      cpx<R> w = twm(ay, n);
+      w.y *= isg;
+      e[m] = x;
+      o[m] = cmul(x, w);
+    }
+    block_fft2_regs<R, LOG2N>(e, o, buf_e, buf_o, t, stw, cj != 0);
+    if (valid) {
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
-        const int n = t + G * m;
-        cpx<R> x = valid ? B[Tile<R>::at(n, col, ldqB)] : mk<R>(R(0), R(0));
-        if (par) {
-          cpx<R> w = twm(ay, n);
-          w.y *= isg;
-          x = cmul(x, w);
-        }
-        v[m] = x;
-      }
-      block_fft_regs<R, LOG2N>(v, buf, t, stw, cj != 0);
-      if (valid) {
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          const int q = 2 * (t + G * m) + par;
-          const int s = q < N ? q : q - M;
-          if (s >= -Q && s <= Q) Bband[size_t(col) * ldq + s + Q] = v[m];
-        }
+        const int q = 2 * (t + G * m);
+        const int se = q < N ? q : q - M;
+        const int so = q + 1 < N ? q + 1 : q + 1 - M;
+        if (se >= -Q && se <= Q) Bband[size_t(col) * ldq + se + Q] = e[m];
+        if (so >= -Q && so <= Q) Bband[size_t(col) * ldq + so + Q] = o[m];
       }
     }
   }
@@ -676,6 +678,8 @@ void launch_spread(int cfg, const Members& mem, const WsOff& off, const PlanTabl
 }
 
 // ---------------------------------------------------------------------------
+// Inverse band columns: the even and odd rows of each band column of S go
+// through one paired inverse transform; T = even + e^{+2 pi i n/M} odd, n < N.
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
 k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs<R> ay, int cj) {
@@ -687,8 +691,8 @@ k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs
   copy_to_smem(stw, ay.stw, GG::STW);
   const int tid = threadIdx.x;
   const int cl = tid / G, t = tid - cl * G;
-  cpx<R>* buf = sm + cl * FB;
-  cpx<R>* held = sm + CC * FB + cl * N;
+  cpx<R>* buf_e = sm + (2 * cl) * FB;
+  cpx<R>* buf_o = buf_e + FB;
   const int items = (ncols + CC - 1) / CC;
 #pragma unroll 1
   for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
@@ -698,27 +702,23 @@ k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs
     cpx<R>* __restrict__ St = ws_ptr<cpx<R>>(mb, off.B);
     const int col = item * CC + cl;
     const bool valid = col < ncols;
-#pragma unroll 1
-    for (int par = 0; par < 2; ++par) {
-      cpx<R> v[16];
+    cpx<R> e[16], o[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int q = 2 * (t + G * m);
+      const int se = q < N ? q : q - M;
+      const int so = q + 1 < N ? q + 1 : q + 1 - M;
+      const cpx<R> z = mk<R>(R(0), R(0));
+      e[m] = (valid && se >= -Q && se <= Q) ? Sband[size_t(col) * ldq + se + Q] : z;
+      o[m] = (valid && so >= -Q && so <= Q) ? Sband[size_t(col) * ldq + so + Q] : z;
+    }
+    block_fft2_regs<R, LOG2N>(e, o, buf_e, buf_o, t, stw, cj == 0);
+    if (valid) {
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
-        const int q = 2 * (t + G * m) + par;
-        const int s = q < N ? q : q - M;
-        v[m] = (valid && s >= -Q && s <= Q) ? Sband[size_t(col) * ldq + s + Q] : mk<R>(R(0), R(0));
-      }
-      block_fft_regs<R, LOG2N>(v, buf, t, stw, cj == 0);
-      if (par == 0) {
-#pragma unroll
-        for (int m = 0; m < 16; ++m) held[t + G * m] = v[m];
-      } else if (valid) {
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          const int n = t + G * m;
-          const cpx<R> w = twm(ay, n);
-          const cpx<R> e = held[n];
-          St[Tile<R>::at(n, col, ldqB)] = cj ? e + cmul(v[m], w) : e + cmulc(v[m], w);
-        }
+        const int n = t + G * m;
+        const cpx<R> w = twm(ay, n);
+        St[Tile<R>::at(n, col, ldqB)] = cj ? e[m] + cmul(o[m], w) : e[m] + cmulc(o[m], w);
       }
     }
   }

@@ -57,12 +57,12 @@ cudaError_t prepare_cols(PlanGeom& g) {
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   if ((e = cudaFuncSetAttribute(k_col_main<R, L2, false>, A, int(GG::smem_col_main)))) return e;
   if ((e = cudaFuncSetAttribute(k_col_main<R, L2, true>, A, int(GG::smem_col_main)))) return e;
-  if ((e = cudaFuncSetAttribute(k_band_fwd<R, L2>, A, int(GG::smem_band_fwd)))) return e;
+  if ((e = cudaFuncSetAttribute(k_band_fwd<R, L2>, A, int(GG::smem_col)))) return e;
   if ((e = cudaFuncSetAttribute(k_band_inv<R, L2>, A, int(GG::smem_col)))) return e;
   if ((e = g.m_generic ? resident_ctas(k_col_main<R, L2, true>, GG::T_C, GG::smem_col_main, &g.cap_col)
                        : resident_ctas(k_col_main<R, L2, false>, GG::T_C, GG::smem_col_main, &g.cap_col)))
     return e;
-  if ((e = resident_ctas(k_band_fwd<R, L2>, GG::T_C, GG::smem_band_fwd, &g.cap_bandf))) return e;
+  if ((e = resident_ctas(k_band_fwd<R, L2>, GG::T_C, GG::smem_col, &g.cap_bandf))) return e;
   return resident_ctas(k_band_inv<R, L2>, GG::T_C, GG::smem_col, &g.cap_bandi);
 }
 
@@ -225,7 +225,7 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
 #define DSNU_BANDF(L2)                                                                              \
   k_band_fwd<R, L2><<<persistent_grid(nm * ((g.Q + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC),       \
                                       g.cap_bandf),                                                  \
-                      Geo<R, L2>::T_C, Geo<R, L2>::smem_band_fwd, st>>>(mem, off, ldqB, g.Q + 1, L.ldq, \
+                      Geo<R, L2>::T_C, Geo<R, L2>::smem_col, st>>>(mem, off, ldqB, g.Q + 1, L.ldq, \
                                                                          g.Q, ay, cj)
 #define DSNU_BANDI(L2)                                                                              \
   k_band_inv<R, L2><<<persistent_grid(nm * ((g.Q + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC),       \
