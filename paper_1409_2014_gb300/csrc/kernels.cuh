@@ -57,6 +57,9 @@
 #ifndef DSNU_COL_PAIRED
 #define DSNU_COL_PAIRED 1
 #endif
+#ifndef DSNU_COL_REGPF
+#define DSNU_COL_REGPF 1
+#endif
 #ifndef DSNU_TILE_LT32
 #define DSNU_TILE_LT32 2
 #endif
@@ -338,8 +341,23 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
     __syncthreads();
   }
   const int items = (ncols + CC - 1) / CC;
+  const int total = items * mem.count;
+  // the next item's column values are loaded into registers before the
+  // current item's inverse transform (PF), hiding their latency
+  constexpr bool PF = TAB && DSNU_COL_REGPF;
+  cpx<R> xn[PF ? 16 : 1];
+  auto load_col = [&](int it2, cpx<R>(&x)[PF ? 16 : 1]) {
+    const int mi2 = it2 / items;
+    const int col2 = (it2 - mi2 * items) * CC + cl;
+    const cpx<R>* A2 = ws_ptr<cpx<R>>(member_at(mem, mi2), off.A);
+#pragma unroll
+    for (int m = 0; m < (PF ? 16 : 1); ++m)
+      x[m] = (col2 < ncols) ? A2[Tile<R>::at(t + G * m, col2, ldqA)] : mk<R>(R(0), R(0));
+  };
+  if constexpr (PF)
+    if (int(blockIdx.x) < total) load_col(blockIdx.x, xn);
 #pragma unroll 1
-  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const int mi = it / items, item = it - mi * items;
     cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(member_at(mem, mi), off.A);
     const int col = item * CC + cl;
@@ -351,7 +369,9 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int n = t + G * m;
-      const cpx<R> x = valid ? A[Tile<R>::at(n, col, ldqA)] : mk<R>(R(0), R(0));
+      cpx<R> x;
+      if constexpr (PF) x = xn[m];
+      else x = valid ? A[Tile<R>::at(n, col, ldqA)] : mk<R>(R(0), R(0));
       cpx<R> w;
       if constexpr (TAB) w = wtab[n];
       else w = twm(ay, n);
@@ -381,6 +401,8 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
         o[m] = o[m] * (valid ? mult_high<GEN>(mt, wx2, kxc, gx, q + 1) : R(0));
       }
     }
+    if constexpr (PF)
+      if (it + int(gridDim.x) < total) load_col(it + gridDim.x, xn);
     block_fft2_regs<R, LOG2N>(e, o, buf_e, buf_o, t, stw, cj == 0);
     if (valid) {
 #pragma unroll
