@@ -398,11 +398,25 @@ __device__ __forceinline__ R expm1_r(R x) {
   else return expm1(x);
 }
 
-// a / b: fast reciprocal path in FP32 (<= 2 ulp), IEEE division in FP64.
+// 1/b in FP64 by Newton-Raphson: the hardware's approximate reciprocal
+// (rcp.approx.ftz.f64, about 2^-20 relative) refined twice by
+// r <- r + r (1 - b r), which squares the relative error each step, so the
+// result is within a couple of ulp of 1/b.  Five FP64 operations instead of
+// an IEEE division; b must be a normal number (here b >= dk^2 > 0).
+__device__ __forceinline__ double rcp_nr(double b) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+  double e = fma(-b, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-b, r, 1.0);
+  return fma(r, e, r);
+}
+
+// a / b: fast reciprocal path in FP32 (<= 2 ulp), a * rcp_nr(b) in FP64.
 template <typename R>
 __device__ __forceinline__ R fdiv(R a, R b) {
   if constexpr (sizeof(R) == 4) return __fdividef(a, b);
-  else return a / b;
+  else return a * rcp_nr(b);
 }
 
 }  // namespace dsnu
