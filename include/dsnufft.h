@@ -182,6 +182,27 @@ const char* dsnu_last_error(void);
 dsnu_status dsnu_solve_host(dsnu_plan plan, const double* rho_host, double* phi_host,
                             double* rho_dev, double* phi_dev, void* stream);
 
+/* Many host densities through one plan with the copies overlapped (the
+ * streaming form of dsnu_solve_host): for i = 0 .. count-1, rho_host[i] is
+ * copied into one of two device staging slots, solved on `stream`, and the
+ * result copied back to phi_host[i].  The upload of density i+1 and the
+ * download of result i-1 run on two copy streams owned by the plan while
+ * density i is solved.  rho_host[i], phi_host[i]: host arrays of ny*nx
+ * doubles ([ny][nx]); pinned memory (cudaHostAlloc / cudaHostRegister) keeps
+ * the copies asynchronous; a buffer may appear several times (a phi_host
+ * buffer receives the results in order).  staging_dev: caller-owned device
+ * memory of at least dsnu_stream_staging_bytes(plan) bytes, 256-byte aligned
+ * (two density and two potential slots).  The solves use the plan's
+ * workspace.  Asynchronous: on return everything is enqueued and `stream` is
+ * ordered after the last download, so synchronising `stream` completes the
+ * batch; the caller must not touch the host or staging buffers before that.
+ * Errors: DSNU_EINVAL (NULL arguments, count < 1, staging too small or
+ * misaligned, no workspace), DSNU_ECUDA. */
+size_t dsnu_stream_staging_bytes(dsnu_plan plan);
+dsnu_status dsnu_solve_host_stream(dsnu_plan plan, int32_t count, const double* const* rho_host,
+                                   double* const* phi_host, void* staging_dev, size_t staging_bytes,
+                                   void* stream);
+
 /* Per-kernel timing.  After dsnu_profile_begin(plan, max_solves), each of the
  * next max_solves solves of this plan records CUDA events on its stream
  * before its first kernel and after each of its dsnu_stage_count() kernels.
@@ -193,7 +214,6 @@ dsnu_status dsnu_solve_host(dsnu_plan plan, const double* rho_host, double* phi_
 dsnu_status dsnu_profile_begin(dsnu_plan plan, int max_solves);
 dsnu_status dsnu_profile_end(dsnu_plan plan, double* stage_ms, int n_stages, int* n_solves);
 
-/* Number of kernels one solve launches, and their names (static strings). */
 /* The radial rule of the polar quadrature (eq. I2PolarDisc), host only, no
  * device needed: n_r nodes r[i] in (0, cut_radius), ascending, and weights
  * w[i] with sum_i w[i] f(r[i]) ~ int_0^P f(r) r dr (the polar Jacobian
@@ -217,6 +237,7 @@ dsnu_status dsnu_radial_nodes(int32_t n_r, int32_t rule, double cut_radius, doub
 dsnu_status dsnu_params_auto(int32_t nx, int32_t ny, double lx, double ly, double eps, int32_t precision,
                              dsnu_params* out);
 
+/* Number of kernels one solve launches, and their names (static strings). */
 int32_t dsnu_stage_count(void);
 const char* dsnu_stage_name(int32_t stage);
 

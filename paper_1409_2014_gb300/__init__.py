@@ -137,6 +137,30 @@ class Plan:
                         phi_dev.data_ptr(), stream)
         return phi_host
 
+    def solve_host_stream(self, rho_hosts, phi_hosts):
+        """Streams host densities through the plan with overlapped copies
+        (dsnu_solve_host_stream): rho_hosts[i] -> phi_hosts[i], contiguous
+        float64 CPU tensors of the grid shape (pinned for asynchronous copies);
+        a tensor may appear several times.  Asynchronous on the current stream
+        (synchronise before reading the results).  The device staging (four
+        grid-sized slots) is allocated once and kept by the plan object."""
+        import torch
+
+        if len(rho_hosts) != len(phi_hosts) or not rho_hosts:
+            raise ValueError("rho_hosts and phi_hosts must have the same, non-zero length")
+        for t in list(rho_hosts) + list(phi_hosts):
+            if t.device.type != "cpu" or t.dtype != torch.float64 or tuple(t.shape) != self.shape \
+                    or not t.is_contiguous():
+                raise ValueError("host buffers must be contiguous float64 CPU tensors of the grid shape")
+        nbytes = _abi.dsnu_stream_staging_bytes(self._handle)
+        if getattr(self, "_staging", None) is None or self._staging.numel() < nbytes:
+            self._staging = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        _abi.dsnu_solve_host_stream(self._handle, [t.data_ptr() for t in rho_hosts],
+                                    [t.data_ptr() for t in phi_hosts], self._staging.data_ptr(),
+                                    self._staging.numel(), stream)
+        return phi_hosts
+
     def profile_begin(self, max_solves: int) -> None:
         dsnu_profile_begin(self._handle, max_solves)
 

@@ -30,7 +30,7 @@ EXPORTED = [
     "dsnu_ds_nonlinear", "dsnu_ds_nonlinear_vjp", "dsnu_ds_nonlinear_vjp_finish", "dsnu_ds_plan_destroy",
     "dsnu_batch_create", "dsnu_batch_workspace_bytes", "dsnu_batch_bind", "dsnu_batch_capture_graph",
     "dsnu_batch_solve", "dsnu_batch_destroy", "dsnu_radial_nodes", "dsnu_params_auto",
-    "dsnu_plan_create_multiplier",
+    "dsnu_plan_create_multiplier", "dsnu_stream_staging_bytes", "dsnu_solve_host_stream",
 ]
 
 
@@ -121,6 +121,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dsnu_plan_create_multiplier.argtypes = [ctypes.POINTER(dsnu_params), ctypes.POINTER(dsnu_multiplier), vp,
                                                 ctypes.POINTER(vp)]
     lib.dsnu_plan_create_multiplier.restype = st
+    lib.dsnu_stream_staging_bytes.argtypes = [vp]
+    lib.dsnu_stream_staging_bytes.restype = ctypes.c_size_t
+    lib.dsnu_solve_host_stream.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(vp), ctypes.POINTER(vp), vp,
+                                           ctypes.c_size_t, vp]
+    lib.dsnu_solve_host_stream.restype = st
     lib.dsnu_params_auto.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_int32, ctypes.POINTER(dsnu_params)]
     lib.dsnu_params_auto.restype = st
@@ -255,6 +260,20 @@ def dsnu_params_auto(nx: int, ny: int, lx: float, ly: float, eps: float, precisi
     _check(load().dsnu_params_auto(int(nx), int(ny), float(lx), float(ly), float(eps), int(precision),
                                    ctypes.byref(out)), "dsnu_params_auto")
     return out
+
+
+def dsnu_stream_staging_bytes(plan: int) -> int:
+    return int(load().dsnu_stream_staging_bytes(ctypes.c_void_p(plan)))
+
+
+def dsnu_solve_host_stream(plan: int, rho_hosts, phi_hosts, staging: int, staging_bytes: int,
+                           stream: int = 0) -> None:
+    n = len(rho_hosts)
+    ra = (ctypes.c_void_p * n)(*[ctypes.c_void_p(p) for p in rho_hosts])
+    pa = (ctypes.c_void_p * n)(*[ctypes.c_void_p(p) for p in phi_hosts])
+    _check(load().dsnu_solve_host_stream(ctypes.c_void_p(plan), n, ra, pa, ctypes.c_void_p(staging),
+                                         ctypes.c_size_t(staging_bytes), ctypes.c_void_p(stream)),
+           "dsnu_solve_host_stream")
 
 
 def dsnu_stage_count() -> int:

@@ -127,4 +127,9 @@ struct dsnu_plan_s {
   size_t ws_bytes;
   cudaEvent_t* prof_events; // profiling: max_solves * kProfEvents events, or NULL
   int prof_max, prof_used;
+  // streaming host solves (dsnu_solve_host_stream): two copy streams and the
+  // per-slot events, created on first use
+  bool has_copy_streams;
+  cudaStream_t copy_in, copy_out;
+  cudaEvent_t ev_start, ev_in[2], ev_solved[2], ev_out[2];
 };

@@ -793,6 +793,18 @@ dsnu_status dsnu_status_poll(dsnu_plan plan, void* stream) {
 dsnu_status dsnu_plan_destroy(dsnu_plan plan) {
   if (!plan) return DSNU_OK;
   free_profile(plan);
+  if (plan->has_copy_streams) {
+    cudaStreamSynchronize(plan->copy_in);
+    cudaStreamSynchronize(plan->copy_out);
+    cudaStreamDestroy(plan->copy_in);
+    cudaStreamDestroy(plan->copy_out);
+    cudaEventDestroy(plan->ev_start);
+    for (int k = 0; k < 2; ++k) {
+      cudaEventDestroy(plan->ev_in[k]);
+      cudaEventDestroy(plan->ev_solved[k]);
+      cudaEventDestroy(plan->ev_out[k]);
+    }
+  }
   if (plan->spread_block) cudaFree(plan->spread_block);
   cudaError_t e = cudaFree(plan->table_block);
   delete plan;
@@ -812,6 +824,69 @@ dsnu_status dsnu_solve_host(dsnu_plan plan, const double* rho_host, double* phi_
   if (s != DSNU_OK) return s;
   e = cudaMemcpyAsync(phi_host, phi_dev, nbytes, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return fail(DSNU_ECUDA, std::string("D2H copy: ") + cudaGetErrorString(e));
+  return DSNU_OK;
+}
+
+size_t dsnu_stream_staging_bytes(dsnu_plan plan) {
+  return plan ? 4 * ((size_t(plan->geom.nx) * plan->geom.ny * sizeof(double) + 255) & ~size_t(255)) : 0;
+}
+
+static cudaError_t make_copy_streams(dsnu_plan p) {
+  if (p->has_copy_streams) return cudaSuccess;
+  cudaError_t e = cudaStreamCreateWithFlags(&p->copy_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->copy_out, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&p->ev_in[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_solved[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_out[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) p->has_copy_streams = true;
+  return e;
+}
+
+dsnu_status dsnu_solve_host_stream(dsnu_plan plan, int32_t count, const double* const* rho_host,
+                                   double* const* phi_host, void* staging_dev, size_t staging_bytes,
+                                   void* stream) {
+  if (!plan) return fail(DSNU_EINVAL, "NULL plan");
+  if (count < 1 || !rho_host || !phi_host || !staging_dev) return fail(DSNU_EINVAL, "count >= 1 and buffers required");
+  for (int i = 0; i < count; ++i)
+    if (!rho_host[i] || !phi_host[i]) return fail(DSNU_EINVAL, "NULL host buffer");
+  if (staging_bytes < dsnu_stream_staging_bytes(plan)) return fail(DSNU_EINVAL, "staging buffer too small");
+  if (reinterpret_cast<uintptr_t>(staging_dev) & 255) return fail(DSNU_EINVAL, "staging must be 256-byte aligned");
+  if (!plan->ws) return fail(DSNU_EINVAL, "no workspace attached (dsnu_set_workspace)");
+  cudaError_t e = make_copy_streams(plan);
+  if (e != cudaSuccess) return fail(DSNU_ECUDA, std::string("copy streams: ") + cudaGetErrorString(e));
+  const size_t nbytes = size_t(plan->geom.nx) * plan->geom.ny * sizeof(double);
+  const size_t slot = (nbytes + 255) & ~size_t(255);
+  char* base = static_cast<char*>(staging_dev);
+  double* rho_s[2] = {reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + slot)};
+  double* phi_s[2] = {reinterpret_cast<double*>(base + 2 * slot), reinterpret_cast<double*>(base + 3 * slot)};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the copy streams start after the caller's earlier work on `stream`
+  e = cudaEventRecord(plan->ev_start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->copy_in, plan->ev_start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->copy_out, plan->ev_start, 0);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    const int k = i & 1;
+    // slot k's density is free once solve i-2 has read it
+    if (i >= 2) e = cudaStreamWaitEvent(plan->copy_in, plan->ev_solved[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rho_s[k], rho_host[i], nbytes, cudaMemcpyHostToDevice, plan->copy_in);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_in[k], plan->copy_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, plan->ev_in[k], 0);
+    // slot k's potential is free once download i-2 has finished
+    if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(st, plan->ev_out[k], 0);
+    if (e != cudaSuccess) break;
+    const dsnu_status s = run(plan, rho_s[k], phi_s[k], stream, 0);
+    if (s != DSNU_OK) return s;
+    e = cudaEventRecord(plan->ev_solved[k], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->copy_out, plan->ev_solved[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(phi_host[i], phi_s[k], nbytes, cudaMemcpyDeviceToHost, plan->copy_out);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->ev_out[k], plan->copy_out);
+  }
+  // `stream` is ordered after every download (the last one covers the others)
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, plan->ev_out[(count - 1) & 1], 0);
+  if (e != cudaSuccess) return fail(DSNU_ECUDA, std::string("streamed solve: ") + cudaGetErrorString(e));
   return DSNU_OK;
 }
 

@@ -144,6 +144,13 @@ def test_bad_multiplier_is_rejected(lib, alpha, a0):
     assert ei.value.status == _abi.DSNU_EINVAL
 
 
+def test_stream_solve_rejects_bad_arguments(lib):
+    assert lib.dsnu_stream_staging_bytes(None) == 0
+    vp = ctypes.c_void_p
+    arr = (vp * 1)(vp(1))
+    assert lib.dsnu_solve_host_stream(None, 1, arr, arr, vp(256), 1 << 20, None) == _abi.DSNU_EINVAL
+
+
 def test_null_plan_calls(lib):
     assert lib.dsnu_workspace_bytes(None) == 0
     assert lib.dsnu_solve(None, None, None, None) == _abi.DSNU_EINVAL
