@@ -373,6 +373,18 @@ __device__ __forceinline__ void block_fft2_regs(cpx<R> (&a)[16], cpx<R> (&b)[16]
   }
 }
 
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may start while its predecessor in the stream is still
+// running: grid_dep_wait() blocks until the predecessor has completed and its
+// writes are visible (a no-op for a normally launched kernel), so a kernel
+// touches only its constant plan tables and shared memory before it.
+// grid_dep_trigger() lets the successor launch once every CTA has called it
+// or exited.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // Cooperative copy of `n` table entries from global to shared memory.
 template <typename T>
 __device__ __forceinline__ void copy_to_smem(T* __restrict__ dst, const T* __restrict__ src, int n) {

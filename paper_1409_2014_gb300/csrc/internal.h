@@ -74,6 +74,7 @@ struct PlanGeom {
   int spread_tile;         // its tile edge (cells)
   int precision, sharp;
   int standard;  // 1: the standard periodic FFT solver (kappa = 1, p = 0; standard.cuh)
+  int pdl;       // 1: pipeline kernels launched with programmatic dependent launch
   // multiplier |k|^alpha (a0 + ac cos 2theta + as sin 2theta) when m_generic (else -k_x^2/|k|^2)
   int m_generic, m_alpha;
   double m_a0, m_ac, m_as;

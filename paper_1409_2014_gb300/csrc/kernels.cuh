@@ -238,6 +238,7 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   if constexpr (GG::ROW_TAB)
     for (int i = threadIdx.x; i < N; i += T) wtab[i] = twm(ax, i);
   __syncthreads();
+  grid_dep_wait();
   const int tid = threadIdx.x;
   const int rr = GG::ILV_F ? (tid & 1) : tid / G;
   const int t = GG::ILV_F ? (tid >> 1) : tid - rr * G;
@@ -247,6 +248,7 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   const int items = (ny + RB - 1) / RB;
 #pragma unroll 1
   for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+    if (it + int(gridDim.x) >= items * mem.count) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     const Member mb = member_at(mem, mi);
     const double* __restrict__ rho = mb.rho;
@@ -340,6 +342,7 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
     }
     __syncthreads();
   }
+  grid_dep_wait();
   const int items = (ncols + CC - 1) / CC;
   const int total = items * mem.count;
   // the next item's column values are loaded into registers before the
@@ -358,6 +361,7 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
     if (int(blockIdx.x) < total) load_col(blockIdx.x, xn);
 #pragma unroll 1
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    if (it + int(gridDim.x) >= total) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(member_at(mem, mi), off.A);
     const int col = item * CC + cl;
@@ -438,6 +442,7 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
   const R isg = cj ? R(-1) : R(1);
   cpx<R>* buf = sm + cl * FB;
   cpx<R>* held = sm + CC * FB + cl * N;  // even-chain result, index n
+  grid_dep_wait();
   const int items = (ncols + CC - 1) / CC;
 #pragma unroll 1
   for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
@@ -505,8 +510,10 @@ k_band_fwd(Members mem, WsOff off, int ldqB, int ncols, int ldq, int Q, AxisTabs
   cpx<R>* buf_e = sm + (2 * cl) * FB;
   cpx<R>* buf_o = buf_e + FB;
   const int items = (ncols + CC - 1) / CC;
+  grid_dep_wait();
 #pragma unroll 1
   for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+    if (it + int(gridDim.x) >= items * mem.count) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     const Member mb = member_at(mem, mi);
     const cpx<R>* __restrict__ B = ws_ptr<cpx<R>>(mb, off.B);
@@ -543,6 +550,7 @@ template <typename R>
 __global__ void __launch_bounds__(256)
 k_interp(Members mem, WsOff off, int ldq, int Q, const int2* __restrict__ q0,
          const R* __restrict__ wts, const double* __restrict__ D, int n_nodes, int w, int cj) {
+  grid_dep_wait();
   const Member mb = member_at(mem, blockIdx.y);
   const cpx<R>* __restrict__ Bband = ws_ptr<cpx<R>>(mb, off.Bband);
   cpx<R>* __restrict__ c = ws_ptr<cpx<R>>(mb, off.c);
@@ -605,6 +613,7 @@ k_spread(Members mem, WsOff off, const int2* __restrict__ item_range,
   __shared__ cpx<R> s_c[CHUNK];
   __shared__ R s_w[CHUNK * 32];
   __shared__ R s_red[2][SPLIT][CELLS];
+  grid_dep_wait();
   const Member mb = member_at(mem, blockIdx.y);
   const cpx<R>* __restrict__ c = ws_ptr<cpx<R>>(mb, off.c);
   cpx<R>* __restrict__ partial = ws_ptr<cpx<R>>(mb, off.partial);
@@ -655,6 +664,7 @@ __global__ void __launch_bounds__(TILE * TILE)
 k_spread_reduce(Members mem, WsOff off, const int* __restrict__ tile_items, int tiles_x,
                 int n_tiles, int Q, int ldq, int cj) {
   constexpr int CELLS = TILE * TILE;
+  grid_dep_wait();
   const Member mb = member_at(mem, blockIdx.y);
   const cpx<R>* __restrict__ partial = ws_ptr<cpx<R>>(mb, off.partial);
   cpx<R>* __restrict__ Sband = ws_ptr<cpx<R>>(mb, off.Sband);
@@ -678,18 +688,34 @@ k_spread_reduce(Members mem, WsOff off, const int* __restrict__ tile_items, int 
 
 // Launch the spreading pair with configuration `cfg`: part 0 = k_spread,
 // part 1 = k_spread_reduce, part 2 = both.
+// Launch with programmatic stream serialization when `pdl` (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+inline void launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <typename R>
 void launch_spread(int cfg, const Members& mem, const WsOff& off, const PlanTables& t, const PlanGeom& g,
-                   int ldq, int cj, cudaStream_t st, int part) {
+                   int ldq, int cj, cudaStream_t st, int part, bool pdl) {
   const R* ew = static_cast<const R*>(t.ent_w);
 #define DSNU_SPREAD(TL, SP, CH)                                                                     \
   if (part != 1 && g.n_items > 0)                                                                 \
-    k_spread<R, TL, SP, CH><<<dim3(g.n_items, mem.count), TL * TL * SP, 0, st>>>(                   \
-        mem, off, t.item_range, t.ent_node, t.ent_q0, ew, t.item_tile, g.w, g.tiles_x, g.Q);         \
+    launch_k(pdl, k_spread<R, TL, SP, CH>, dim3(g.n_items, mem.count), dim3(TL * TL * SP), 0, st,  \
+             mem, off, t.item_range, t.ent_node, t.ent_q0, ew, t.item_tile, g.w, g.tiles_x, g.Q);    \
   if (part != 0)                                                                                    \
-    k_spread_reduce<R, TL><<<dim3(g.n_tiles, mem.count), TL * TL, 0, st>>>(mem, off, t.tile_items,  \
-                                                                          g.tiles_x, g.n_tiles, g.Q, \
-                                                                          ldq, cj)
+    launch_k(pdl, k_spread_reduce<R, TL>, dim3(g.n_tiles, mem.count), dim3(TL * TL), 0, st, mem, off, \
+             t.tile_items, g.tiles_x, g.n_tiles, g.Q, ldq, cj)
   switch (cfg) {
     case 1: DSNU_SPREAD(8, 2, 128); break;
     case 2: DSNU_SPREAD(16, 1, 128); break;
@@ -716,8 +742,10 @@ k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs
   cpx<R>* buf_e = sm + (2 * cl) * FB;
   cpx<R>* buf_o = buf_e + FB;
   const int items = (ncols + CC - 1) / CC;
+  grid_dep_wait();
 #pragma unroll 1
   for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+    if (it + int(gridDim.x) >= items * mem.count) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     const Member mb = member_at(mem, mi);
     const cpx<R>* __restrict__ Sband = ws_ptr<cpx<R>>(mb, off.Sband);
@@ -766,6 +794,7 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   if constexpr (GG::ROW_TAB)
     for (int i = threadIdx.x; i < N; i += GG::T_RI) wtab[i] = twm(ax, i);
   __syncthreads();
+  grid_dep_wait();
   const int tid = threadIdx.x;
   const int rr = GG::ILV_I ? (tid & 1) : tid / G;
   const int t = GG::ILV_I ? (tid >> 1) : tid - rr * G;
@@ -775,6 +804,7 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   const int items = (ny + RB - 1) / RB;
 #pragma unroll 1
   for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+    if (it + int(gridDim.x) >= items * mem.count) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     const Member mb = member_at(mem, mi);
     const cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(mb, off.A);

@@ -207,36 +207,31 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
   const long nm = mem.count;
 
 #define DSNU_ROWF(L2)                                                                               \
-  k_row_fwd<R, L2><<<persistent_grid(nm * ((g.ny + Geo<R, L2>::RB_F - 1) / Geo<R, L2>::RB_F),       \
-                                     g.cap_rowf),                                                    \
-                     Geo<R, L2>::T_RF, Geo<R, L2>::smem_row_fwd, st>>>(mem, off, ldqA, ldqB, g.Q,    \
-                                                                       g.ny, ax, dcy, cj)
+  launch_k(g.pdl != 0, k_row_fwd<R, L2>,                                                            \
+           dim3(persistent_grid(nm * ((g.ny + Geo<R, L2>::RB_F - 1) / Geo<R, L2>::RB_F), g.cap_rowf)), \
+           dim3(Geo<R, L2>::T_RF), Geo<R, L2>::smem_row_fwd, st, mem, off, ldqA, ldqB, g.Q, g.ny, ax, dcy, cj)
 #define DSNU_COLM(L2)                                                                               \
   if (g.m_generic)                                                                                  \
-    k_col_main<R, L2, true><<<persistent_grid(nm * ((g.nx + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC), \
-                                              g.cap_col),                                           \
-                              Geo<R, L2>::T_C, Geo<R, L2>::smem_col_main, st>>>(mem, off, ldqA, g.nx + 1, \
-                                                                                ay, mt, cj);        \
+    launch_k(g.pdl != 0, k_col_main<R, L2, true>,                                                   \
+             dim3(persistent_grid(nm * ((g.nx + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC), g.cap_col)), \
+             dim3(Geo<R, L2>::T_C), Geo<R, L2>::smem_col_main, st, mem, off, ldqA, g.nx + 1, ay, mt, cj); \
   else                                                                                              \
-    k_col_main<R, L2, false><<<persistent_grid(nm * ((g.nx + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC), \
-                                               g.cap_col),                                          \
-                               Geo<R, L2>::T_C, Geo<R, L2>::smem_col_main, st>>>(mem, off, ldqA,      \
-                                                                                 g.nx + 1, ay, mt, cj)
+    launch_k(g.pdl != 0, k_col_main<R, L2, false>,                                                  \
+             dim3(persistent_grid(nm * ((g.nx + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC), g.cap_col)), \
+             dim3(Geo<R, L2>::T_C), Geo<R, L2>::smem_col_main, st, mem, off, ldqA, g.nx + 1, ay, mt, cj)
 #define DSNU_BANDF(L2)                                                                              \
-  k_band_fwd<R, L2><<<persistent_grid(nm * ((g.Q + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC),       \
-                                      g.cap_bandf),                                                  \
-                      Geo<R, L2>::T_C, Geo<R, L2>::smem_col, st>>>(mem, off, ldqB, g.Q + 1, L.ldq, \
-                                                                         g.Q, ay, cj)
+  launch_k(g.pdl != 0, k_band_fwd<R, L2>,                                                           \
+           dim3(persistent_grid(nm * ((g.Q + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC), g.cap_bandf)), \
+           dim3(Geo<R, L2>::T_C), Geo<R, L2>::smem_col, st, mem, off, ldqB, g.Q + 1, L.ldq, g.Q, ay, cj)
 #define DSNU_BANDI(L2)                                                                              \
-  k_band_inv<R, L2><<<persistent_grid(nm * ((g.Q + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC),       \
-                                      g.cap_bandi),                                                  \
-                      Geo<R, L2>::T_C, Geo<R, L2>::smem_col, st>>>(mem, off, L.ldq, g.Q, g.Q + 1, ldqB, \
-                                                                    ay, cj)
+  launch_k(g.pdl != 0, k_band_inv<R, L2>,                                                           \
+           dim3(persistent_grid(nm * ((g.Q + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC), g.cap_bandi)), \
+           dim3(Geo<R, L2>::T_C), Geo<R, L2>::smem_col, st, mem, off, L.ldq, g.Q, g.Q + 1, ldqB, ay, cj)
 #define DSNU_ROWI(L2)                                                                               \
-  k_row_inv<R, L2><<<persistent_grid(nm * ((g.ny + Geo<R, L2>::RB_I - 1) / Geo<R, L2>::RB_I),       \
-                                     g.cap_rowi),                                                    \
-                     Geo<R, L2>::T_RI, Geo<R, L2>::smem_row_inv, st>>>(mem, off, ldqA, ldqB, g.Q,    \
-                                                                       g.ny, ax, dcy, R(g.scale), cj)
+  launch_k(g.pdl != 0, k_row_inv<R, L2>,                                                            \
+           dim3(persistent_grid(nm * ((g.ny + Geo<R, L2>::RB_I - 1) / Geo<R, L2>::RB_I), g.cap_rowi)), \
+           dim3(Geo<R, L2>::T_RI), Geo<R, L2>::smem_row_inv, st, mem, off, ldqA, ldqB, g.Q, g.ny, ax, dcy, \
+           R(g.scale), cj)
 #define DSNU_MARK(I) \
   if (ev) cudaEventRecord(ev[I], st)
   DSNU_MARK(0);
@@ -250,12 +245,12 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
     default: return DSNU_EUNSUPPORTED;
   }
   DSNU_MARK(2);
-  k_interp<R><<<dim3((g.n_nodes + 7) / 8, mem.count), 256, 0, st>>>(mem, off, L.ldq, g.Q, t.node_q0, wts,
-                                                                     t.node_D, g.n_nodes, g.w, cj);
+  launch_k(g.pdl != 0, k_interp<R>, dim3((g.n_nodes + 7) / 8, mem.count), dim3(256), 0, st, mem, off, L.ldq, g.Q,
+           t.node_q0, wts, t.node_D, g.n_nodes, g.w, cj);
   DSNU_MARK(3);
-  launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, cj, st, 0);
+  launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, cj, st, 0, g.pdl != 0);
   DSNU_MARK(4);
-  launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, cj, st, 1);
+  launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, cj, st, 1, g.pdl != 0);
   DSNU_MARK(5);
   switch (g.log2ny) {
     DSNU_LOG2_CASES(DSNU_BANDI)
@@ -294,9 +289,9 @@ cudaError_t time_spread(const PlanGeom& g, const PlanTables& t, const WsLayout& 
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) return e;
-  launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, 0, 0, 2);  // warm-up
+  launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, 0, 0, 2, false);  // warm-up
   cudaEventRecord(e0, 0);
-  for (int i = 0; i < reps; ++i) launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, 0, 0, 2);
+  for (int i = 0; i < reps; ++i) launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, 0, 0, 2, false);
   cudaEventRecord(e1, 0);
   e = cudaEventSynchronize(e1);
   float total = 0.f;

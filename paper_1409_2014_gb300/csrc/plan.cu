@@ -690,6 +690,10 @@ dsnu_status dsnu_plan_create_multiplier(const dsnu_params* params, const dsnu_mu
   g.nx = p.nx;
   g.ny = p.ny;
   g.standard = standard ? 1 : 0;
+  {
+    const char* env = std::getenv("DSNU_PDL");  // DSNU_PDL=0: plain stream-ordered launches
+    g.pdl = (env && env[0] == '0') ? 0 : 1;
+  }
   if (mult) {
     g.m_generic = 1;
     g.m_alpha = mult->alpha;
