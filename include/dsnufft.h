@@ -145,6 +145,13 @@ size_t dsnu_workspace_bytes(dsnu_plan plan);
 dsnu_status dsnu_set_workspace(dsnu_plan plan, void* workspace_dev, size_t bytes);
 
 /* Phi = I1 + I2 (Sec. 2.1, eq. PotSplitWhoSpace) for one density.
+ * For mixed plans on grids of at least 2048 x 2048 the band chain (the NUFFT
+ * part) runs on a low-priority stream owned by the plan, concurrently with the
+ * column pass of I1, which then leaves 12 of every 152 SMs free
+ * (DSNU_BAND_SMS=<n> in the environment at plan creation sets the number of
+ * SMs, 0 runs everything on `stream`); the plan orders that stream after
+ * `stream`'s earlier work and `stream` after it, so the call behaves as if
+ * everything ran on `stream`.
  * rho_dev: [ny][nx] FP64 density (device, read only).
  * phi_dev: [ny][nx] FP64 potential (device, written); must not alias rho_dev.
  * Enqueued on `stream` (cudaStream_t or NULL).

@@ -85,10 +85,22 @@ struct PlanGeom {
 constexpr int kStages = 8;       // kernels per solve
 constexpr int kProfEvents = kStages + 1;  // events per profiled solve (see run_pipeline)
 
+// Concurrency of the band chain with the column pass: the band kernels run
+// on `side` (a low-priority stream owned by the plan) while the column pass's
+// persistent grid leaves `reserve` SMs free for them.
+struct Overlap {
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+  int reserve;
+};
+
 // Launchers (one translation unit per precision).  `ev`, when not NULL,
-// holds kProfEvents events recorded around the kernels.
+// holds kProfEvents events recorded around the kernels (the kernels then run
+// one after the other on `st`); `ov`, when not NULL, runs the band chain
+// concurrently with the column pass.
 dsnu_status run_pipeline_f32(const PlanGeom& g, const PlanTables& t, const WsLayout& L,
-                             const Members& mem, cudaStream_t st, int cj, cudaEvent_t* ev);
+                             const Members& mem, cudaStream_t st, int cj, cudaEvent_t* ev,
+                             const Overlap* ov = nullptr);
 // Time one spreading configuration (spread + reduce, `reps` launches) on
 // scratch buffers laid out by L; returns the average milliseconds in *ms.
 cudaError_t time_spread_f32(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws, int reps,
@@ -96,7 +108,8 @@ cudaError_t time_spread_f32(const PlanGeom& g, const PlanTables& t, const WsLayo
 cudaError_t time_spread_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws, int reps,
                             float* ms);
 dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L,
-                             const Members& mem, cudaStream_t st, int cj, cudaEvent_t* ev);
+                             const Members& mem, cudaStream_t st, int cj, cudaEvent_t* ev,
+                             const Overlap* ov = nullptr);
 
 // A single density as a one-member launch.
 inline Members single_member(const double* rho, double* phi, void* ws) {
@@ -133,4 +146,5 @@ struct dsnu_plan_s {
   bool has_copy_streams;
   cudaStream_t copy_in, copy_out;
   cudaEvent_t ev_start, ev_in[2], ev_solved[2], ev_out[2];
+  dsnu::Overlap overlap;    // band chain next to the column pass (reserve 0: off)
 };

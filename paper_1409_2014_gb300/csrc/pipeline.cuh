@@ -189,7 +189,7 @@ dsnu_status run_standard(const PlanGeom& g, const PlanTables& t, const WsLayout&
 
 template <typename R>
 dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout& L, const Members& mem,
-                         cudaStream_t st, int cj, cudaEvent_t* ev) {
+                         cudaStream_t st, int cj, cudaEvent_t* ev, const Overlap* ov) {
   if (g.standard) return run_standard<R>(g, t, L, mem, st, cj, ev);
   const WsOff off{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial};
   const AxisTabs<R> ax{static_cast<const cpx<R>*>(t.stw_x), static_cast<const cpx<R>*>(t.twm_lo_x),
@@ -213,20 +213,20 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
 #define DSNU_COLM(L2)                                                                               \
   if (g.m_generic)                                                                                  \
     launch_k(g.pdl != 0, k_col_main<R, L2, true>,                                                   \
-             dim3(persistent_grid(nm * ((g.nx + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC), g.cap_col)), \
+             dim3(persistent_grid(nm * ((g.nx + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC), capc)), \
              dim3(Geo<R, L2>::T_C), Geo<R, L2>::smem_col_main, st, mem, off, ldqA, g.nx + 1, ay, mt, cj); \
   else                                                                                              \
     launch_k(g.pdl != 0, k_col_main<R, L2, false>,                                                  \
-             dim3(persistent_grid(nm * ((g.nx + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC), g.cap_col)), \
+             dim3(persistent_grid(nm * ((g.nx + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC), capc)), \
              dim3(Geo<R, L2>::T_C), Geo<R, L2>::smem_col_main, st, mem, off, ldqA, g.nx + 1, ay, mt, cj)
 #define DSNU_BANDF(L2)                                                                              \
   launch_k(g.pdl != 0, k_band_fwd<R, L2>,                                                           \
            dim3(persistent_grid(nm * ((g.Q + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC), g.cap_bandf)), \
-           dim3(Geo<R, L2>::T_C), Geo<R, L2>::smem_col, st, mem, off, ldqB, g.Q + 1, L.ldq, g.Q, ay, cj)
+           dim3(Geo<R, L2>::T_C), Geo<R, L2>::smem_col, bst, mem, off, ldqB, g.Q + 1, L.ldq, g.Q, ay, cj)
 #define DSNU_BANDI(L2)                                                                              \
   launch_k(g.pdl != 0, k_band_inv<R, L2>,                                                           \
            dim3(persistent_grid(nm * ((g.Q + 1 + Geo<R, L2>::CC - 1) / Geo<R, L2>::CC), g.cap_bandi)), \
-           dim3(Geo<R, L2>::T_C), Geo<R, L2>::smem_col, st, mem, off, L.ldq, g.Q, g.Q + 1, ldqB, ay, cj)
+           dim3(Geo<R, L2>::T_C), Geo<R, L2>::smem_col, bst, mem, off, L.ldq, g.Q, g.Q + 1, ldqB, ay, cj)
 #define DSNU_ROWI(L2)                                                                               \
   launch_k(g.pdl != 0, k_row_inv<R, L2>,                                                            \
            dim3(persistent_grid(nm * ((g.ny + Geo<R, L2>::RB_I - 1) / Geo<R, L2>::RB_I), g.cap_rowi)), \
@@ -234,32 +234,59 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
            R(g.scale), cj)
 #define DSNU_MARK(I) \
   if (ev) cudaEventRecord(ev[I], st)
+  // the band chain (type-2 columns, interpolation, weighting, spreading,
+  // inverse band columns) on stream bst
+  cudaStream_t bst = st;
+  int capc = g.cap_col;
+  auto band_chain = [&](bool marks) -> dsnu_status {
+    switch (g.log2ny) {
+      DSNU_LOG2_CASES(DSNU_BANDF)
+      default: return DSNU_EUNSUPPORTED;
+    }
+    if (marks) DSNU_MARK(2);
+    launch_k(g.pdl != 0, k_interp<R>, dim3((g.n_nodes + 7) / 8, mem.count), dim3(256), 0, bst, mem, off, L.ldq,
+             g.Q, t.node_q0, wts, t.node_D, g.n_nodes, g.w, cj);
+    if (marks) DSNU_MARK(3);
+    launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, cj, bst, 0, g.pdl != 0);
+    if (marks) DSNU_MARK(4);
+    launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, cj, bst, 1, g.pdl != 0);
+    if (marks) DSNU_MARK(5);
+    switch (g.log2ny) {
+      DSNU_LOG2_CASES(DSNU_BANDI)
+      default: return DSNU_EUNSUPPORTED;
+    }
+    return DSNU_OK;
+  };
+  const bool overlap = ov && ov->reserve > 0 && !ev && g.cap_col > ov->reserve;
   DSNU_MARK(0);
   switch (g.log2nx) {
     DSNU_LOG2_CASES(DSNU_ROWF)
     default: return DSNU_EUNSUPPORTED;
   }
   DSNU_MARK(1);
-  switch (g.log2ny) {
-    DSNU_LOG2_CASES(DSNU_BANDF)
-    default: return DSNU_EUNSUPPORTED;
-  }
-  DSNU_MARK(2);
-  launch_k(g.pdl != 0, k_interp<R>, dim3((g.n_nodes + 7) / 8, mem.count), dim3(256), 0, st, mem, off, L.ldq, g.Q,
-           t.node_q0, wts, t.node_D, g.n_nodes, g.w, cj);
-  DSNU_MARK(3);
-  launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, cj, st, 0, g.pdl != 0);
-  DSNU_MARK(4);
-  launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, cj, st, 1, g.pdl != 0);
-  DSNU_MARK(5);
-  switch (g.log2ny) {
-    DSNU_LOG2_CASES(DSNU_BANDI)
-    default: return DSNU_EUNSUPPORTED;
-  }
-  DSNU_MARK(6);
-  switch (g.log2ny) {
-    DSNU_LOG2_CASES(DSNU_COLM)
-    default: return DSNU_EUNSUPPORTED;
+  if (overlap) {
+    // the column pass keeps all but `reserve` SMs; the band chain runs next
+    // to it on the plan's low-priority side stream; row_inv joins both
+    cudaEventRecord(ov->fork, st);
+    cudaStreamWaitEvent(ov->side, ov->fork, 0);
+    capc = g.cap_col - ov->reserve;
+    switch (g.log2ny) {
+      DSNU_LOG2_CASES(DSNU_COLM)
+      default: return DSNU_EUNSUPPORTED;
+    }
+    bst = ov->side;
+    const dsnu_status sb = band_chain(false);
+    if (sb != DSNU_OK) return sb;
+    cudaEventRecord(ov->join, ov->side);
+    cudaStreamWaitEvent(st, ov->join, 0);
+  } else {
+    const dsnu_status sb = band_chain(true);
+    if (sb != DSNU_OK) return sb;
+    DSNU_MARK(6);
+    switch (g.log2ny) {
+      DSNU_LOG2_CASES(DSNU_COLM)
+      default: return DSNU_EUNSUPPORTED;
+    }
   }
   DSNU_MARK(7);
   switch (g.log2nx) {

@@ -3,8 +3,8 @@
 
 namespace dsnu {
 dsnu_status run_pipeline_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L,
-                             const Members& mem, cudaStream_t st, int cj, cudaEvent_t* ev) {
-  return run_pipeline<double>(g, t, L, mem, st, cj, ev);
+                             const Members& mem, cudaStream_t st, int cj, cudaEvent_t* ev, const Overlap* ov) {
+  return run_pipeline<double>(g, t, L, mem, st, cj, ev, ov);
 }
 cudaError_t prepare_kernels_f64(PlanGeom& g) { return prepare_kernels<double>(g); }
 cudaError_t time_spread_f64(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws, int reps,
