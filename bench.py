@@ -208,8 +208,32 @@ def dist_setup(use_cuda: bool):
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+        if not dist.is_initialized():
+            dist.init_process_group(backend="nccl" if use_cuda else "gloo")
     return world, rank, local
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank solves its own density (independent units, no exchange)."""
+    return WL["seed"] + rank
+
+
+def max_over_ranks(v: float, world: int, device=None) -> float:
+    """The slowest rank's time (the job's time); identity for one process."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, units_per_rank: int, t_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: each rank has a fixed share)."""
+    return world * units_per_rank / t_max
 
 
 def run_reference(args):
@@ -251,7 +275,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def batch_bench(dev, max_over_ranks, barrier, reps=5):
+def batch_bench(dev, max_time, barrier, reps=5):
     """64 seeded densities (4-16 Gaussians) with grids drawn from {256, 512,
     1024, 2048}^2 on [-32,32)^2, P = 8, 64 x 256 nodes: mixed plans in one
     batch replayed as a CUDA graph, versus 64 separate FP64 solves."""
@@ -283,7 +307,7 @@ def batch_bench(dev, max_over_ranks, barrier, reps=5):
                 b.solve()
             e1.record(stream)
             barrier()
-            t = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
+            t = max_time(e0.elapsed_time(e1) / 1000.0)
             out["mixed_graph_batch"] = {"solves_per_s": reps * len(members) / t, "ms_per_batch": 1e3 * t / reps}
             b.close()
         else:
@@ -296,7 +320,7 @@ def batch_bench(dev, max_over_ranks, barrier, reps=5):
                     plans[n].solve(r, f)
             e1.record(stream)
             barrier()
-            t = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
+            t = max_time(e0.elapsed_time(e1) / 1000.0)
             out["fp64_separate"] = {"solves_per_s": reps * len(members) / t, "ms_per_batch": 1e3 * t / reps}
         for p in plans.values():
             p.close()
@@ -316,7 +340,7 @@ def run_ours(args):
 
     build()
     n, L = WL["n"], WL["L"]
-    rho_np = synth.density_abs2(n, n, L, L, WL["seed"] + rank, WL["count"])
+    rho_np = synth.density_abs2(n, n, L, L, replica_seed(rank), WL["count"])
     rho0 = torch.from_numpy(rho_np).to(dev)
     ins = [rho0.clone() for _ in range(N_ROT)]
     outs = [torch.empty_like(rho0) for _ in range(N_ROT)]
@@ -329,10 +353,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        import torch.distributed as dist
+    def max_over_ranks_dev(v: float) -> float:
+        return max_over_ranks(v, world, dev)
 
         t = torch.tensor([v], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -366,8 +388,8 @@ def run_ours(args):
     n_stages = len(stage_ms)
     clk = clocks.summary(tw0, tw1)
     clocks.stop()
-    t_max = max_over_ranks(ms_total / 1000.0)
-    value = world * args.steps / t_max
+    t_max = max_over_ranks_dev(ms_total / 1000.0)
+    value = job_value(world, args.steps, t_max)
     ms_per_step = t_max * 1000.0 / args.steps
     if args.only_timed:
         if rank == 0:
@@ -389,7 +411,7 @@ def run_ours(args):
         plan64.solve(ins[i % N_ROT], outs[i % N_ROT])
     e1.record(stream)
     barrier()
-    t64 = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
+    t64 = max_over_ranks_dev(e0.elapsed_time(e1) / 1000.0)
     value64 = world * k64 / t64
 
     # results of both paths on the first input, for the accuracy check
@@ -409,7 +431,7 @@ def run_ours(args):
             ps.solve(ins[i % N_ROT], outs[i % N_ROT])
         e1.record(stream)
         barrier()
-        ts = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
+        ts = max_over_ranks_dev(e0.elapsed_time(e1) / 1000.0)
         standard[prec] = {"solves_per_s": world * reps / ts, "ms_per_step": ts * 1000.0 / reps, "steps": reps}
         ps.close()
 
@@ -425,7 +447,7 @@ def run_ours(args):
     plan.solve_host_stream([rho_h] * ke, [phi_h] * ke)
     e1.record(stream)
     barrier()
-    te = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
+    te = max_over_ranks_dev(e0.elapsed_time(e1) / 1000.0)
     e2e = {"value": world * ke / te, "unit": "solves/s", "h2d_bytes_per_step": int(rho_h.numel() * 8),
            "d2h_bytes_per_step": int(phi_h.numel() * 8), "steps": ke,
            "api": "dsnu_solve_host_stream (pinned host in/out, copies overlapped with solves)"}
@@ -469,7 +491,7 @@ def run_ours(args):
     }
 
     if not args.no_batch:
-        line["batch"] = batch_bench(dev, max_over_ranks, barrier)
+        line["batch"] = batch_bench(dev, max_over_ranks_dev, barrier)
 
     if rank == 0 and not args.no_cpu_baseline:
         est, phi_ref, desc, _ = oracle_sample(rho_np, 1.0)
