@@ -158,7 +158,7 @@ def kernel_hash() -> str:
 
 
 def algorithmic_bytes(stage: str, n: int, Q: int, csz: int, n_nodes: int, w: int, rsz: int,
-                      n_items: int = 0) -> float:
+                      n_items: int = 0, tile: int = 8) -> float:
     """Bytes one launch of a stage must move at minimum (inputs read once,
     outputs written once), for an n x n grid with band half-width Q."""
     A = csz * n * (n + 1)           # half-spectrum intermediate
@@ -170,8 +170,8 @@ def algorithmic_bytes(stage: str, n: int, Q: int, csz: int, n_nodes: int, w: int
         "col_main": 2 * A,
         "band_fwd": Bc + band,
         "interp": band + nodes,
-        "spread": nodes + n_items * 64 * csz,
-        "spread_reduce": n_items * 64 * csz + band,
+        "spread": nodes + n_items * tile * tile * csz,     # node data in, one partial tile per item out
+        "spread_reduce": n_items * tile * tile * csz + band,
         "band_inv": band + Bc,
         "row_inv": A + Bc + 8 * n * n,
     }[stage])
@@ -460,7 +460,7 @@ def run_ours(args):
     dom = max(avg, key=avg.get)
     peak, peak_src = load_peaks()
     alg = algorithmic_bytes(dom, n, info.band_q, csz, info.n_nodes, info.kernel_width, rsz,
-                            info.n_items)
+                            info.n_items, info.spread_tile)
     achieved = alg / (avg[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
@@ -469,7 +469,12 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": alg, "avg_ms": avg[dom],
                 "traffic": load_traffic(dom, "4096sq_mixed"),
                 "stages_ms": {k: round(v, 5) for k, v in avg.items()},
-                "stage_share": {k: round(v / sum(avg.values()), 4) for k, v in avg.items()}}
+                "stage_share": {k: round(v / sum(avg.values()), 4) for k, v in avg.items()},
+                # every kernel: algorithmic bytes / live duration, as a fraction of the measured peak
+                "hbm_frac_per_kernel": {
+                    k: round(algorithmic_bytes(k, n, info.band_q, csz, info.n_nodes, info.kernel_width, rsz,
+                                               info.n_items, info.spread_tile) / (v * 1e-3) / 1e9 / peak, 4)
+                    for k, v in avg.items() if v > 0}}
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
