@@ -154,9 +154,10 @@ dsnu_status dsnu_set_workspace(dsnu_plan plan, void* workspace_dev, size_t bytes
  * everything ran on `stream`.
  * rho_dev: [ny][nx] FP64 density (device, read only).
  * phi_dev: [ny][nx] FP64 potential (device, written); must not alias rho_dev.
+ * Both 16-byte aligned (every cudaMalloc'd or torch-allocated buffer is).
  * Enqueued on `stream` (cudaStream_t or NULL).
- * Errors: DSNU_EINVAL (NULL/aliased pointers, no workspace), DSNU_ECUDA (a
- * launch failed). */
+ * Errors: DSNU_EINVAL (NULL/aliased/misaligned pointers, no workspace),
+ * DSNU_ECUDA (a launch failed). */
 dsnu_status dsnu_solve(dsnu_plan plan, const double* rho_dev, double* phi_dev, void* stream);
 
 /* Transpose of the discrete operator of dsnu_solve: the same pipeline with
@@ -184,8 +185,8 @@ const char* dsnu_last_error(void);
  * phi_dev -> phi_host, and returns at once; phi_host is valid after the
  * stream is synchronised.  rho_host/phi_host: [ny][nx] FP64 host memory
  * (page-locked for the copies to be asynchronous); rho_dev/phi_dev:
- * caller-owned [ny][nx] FP64 device staging buffers.  Same errors as
- * dsnu_solve. */
+ * caller-owned [ny][nx] FP64 device staging buffers (16-byte aligned).
+ * Same errors as dsnu_solve, returned before anything is enqueued. */
 dsnu_status dsnu_solve_host(dsnu_plan plan, const double* rho_host, double* phi_host,
                             double* rho_dev, double* phi_dev, void* stream);
 
@@ -351,7 +352,7 @@ dsnu_status dsnu_batch_create(int32_t count, const dsnu_plan* plans, dsnu_batch*
 size_t dsnu_batch_workspace_bytes(dsnu_batch b);
 
 /* Bind the members' device buffers: rho_dev[i] (FP64 [ny_i][nx_i], read) and
- * phi_dev[i] (written), and the caller-owned batch workspace (>=
+ * phi_dev[i] (written), both 16-byte aligned, and the caller-owned batch workspace (>=
  * dsnu_batch_workspace_bytes, 256-byte aligned).  Uploads the member tables
  * on `stream` and synchronises it; drops a previously captured graph.
  * Errors: DSNU_EINVAL, DSNU_ECUDA. */

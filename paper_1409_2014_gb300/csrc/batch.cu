@@ -126,6 +126,9 @@ dsnu_status dsnu_batch_bind(dsnu_batch b, const double* const* rho_dev, double* 
   if (reinterpret_cast<uintptr_t>(workspace_dev) & 255) return bfail(DSNU_EINVAL, "workspace must be 256-byte aligned");
   for (int i = 0; i < b->count; ++i)
     if (!rho_dev[i] || !phi_dev[i]) return bfail(DSNU_EINVAL, "NULL member pointer");
+  for (int i = 0; i < b->count; ++i)
+    if ((reinterpret_cast<uintptr_t>(rho_dev[i]) | reinterpret_cast<uintptr_t>(phi_dev[i])) & 15)
+      return bfail(DSNU_EINVAL, "member buffers must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace_dev);
   cudaError_t e = cudaSuccess;

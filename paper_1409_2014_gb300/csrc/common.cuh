@@ -157,6 +157,16 @@ __host__ __device__ constexpr int fft_stage_tw_elems(int log2n) {
   return fft_stage_tw_offset(log2n, (log2n + 3) / 4);
 }
 
+// Compact stage table (the CT form of the transforms below): stage 1 as in
+// the full table, then for the stage with NS = 256 (the third stage of
+// N >= 512, radix RAD = N/256) two factors of (RAD - 1) x 16 entries each,
+//   hi[r][k1] = e^{-2 pi i 16 r k1/(NS RAD)},  lo[r][k0] = e^{-2 pi i r k0/(NS RAD)},
+// whose product is the twiddle of k = 16 k1 + k0: 720 entries at N = 4096
+// instead of 4080.
+__host__ __device__ constexpr int fft_stage_tw_elems_ct(int log2n) {
+  return log2n <= 8 ? fft_stage_tw_elems(log2n) : 15 * 16 + 2 * 16 * ((1 << (log2n - 8)) - 1);
+}
+
 template <int LOG2N, int S>
 struct StageInfo {
   static constexpr int full = LOG2N / 4;
@@ -259,7 +269,7 @@ __device__ __forceinline__ void block_fft_regs(cpx<R> (&v)[16], cpx<R>* buf, int
 // they share the barriers and every twiddle load, and each thread has two
 // independent butterflies in flight per stage.
 // ---------------------------------------------------------------------------
-template <typename R, int LOG2N, int S>
+template <typename R, int LOG2N, int S, bool CT>
 __device__ __forceinline__ void fft2_stage_regs(cpx<R> (&a)[16], cpx<R> (&b)[16], cpx<R>* buf_a,
                                                 cpx<R>* buf_b, int t, const cpx<R>* __restrict__ stw) {
   using SI = StageInfo<LOG2N, S>;
@@ -289,7 +299,16 @@ __device__ __forceinline__ void fft2_stage_regs(cpx<R> (&a)[16], cpx<R> (&b)[16]
   for (int bb = 0; bb < PER; ++bb) {
     const int j = t + bb * G;
     const int k = j & (NS - 1);
-    if constexpr (LOG2NS > 0) {
+    if constexpr (CT && LOG2NS == 8) {  // compact table: w = hi[r][k >> 4] lo[r][k & 15]
+      const cpx<R>* hi = stw + 15 * 16 + (k >> 4);
+      const cpx<R>* lo = stw + 15 * 16 + (RAD - 1) * 16 + (k & 15);
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        const cpx<R> w = cmul(hi[(r - 1) * 16], lo[(r - 1) * 16]);
+        a[bb * RAD + r] = cmul(a[bb * RAD + r], w);
+        b[bb * RAD + r] = cmul(b[bb * RAD + r], w);
+      }
+    } else if constexpr (LOG2NS > 0) {
       const cpx<R>* tws = stw + SI::tw_off + k;
 #pragma unroll
       for (int r = 1; r < RAD; ++r) {
@@ -342,16 +361,17 @@ __device__ __forceinline__ void fft2_stage_regs(cpx<R> (&a)[16], cpx<R> (&b)[16]
   }
 }
 
-template <typename R, int LOG2N, int S>
+template <typename R, int LOG2N, int S, bool CT>
 __device__ __forceinline__ void fft2_stages_regs(cpx<R> (&a)[16], cpx<R> (&b)[16], cpx<R>* buf_a,
                                                  cpx<R>* buf_b, int t, const cpx<R>* __restrict__ stw) {
   if constexpr (S < StageInfo<LOG2N, 0>::nstages) {
-    fft2_stage_regs<R, LOG2N, S>(a, b, buf_a, buf_b, t, stw);
-    fft2_stages_regs<R, LOG2N, S + 1>(a, b, buf_a, buf_b, t, stw);
+    fft2_stage_regs<R, LOG2N, S, CT>(a, b, buf_a, buf_b, t, stw);
+    fft2_stages_regs<R, LOG2N, S + 1, CT>(a, b, buf_a, buf_b, t, stw);
   }
 }
 
-template <typename R, int LOG2N>
+// CT = true: `stw` is the compact stage table (fft_stage_tw_elems_ct).
+template <typename R, int LOG2N, bool CT = false>
 __device__ __forceinline__ void block_fft2_regs(cpx<R> (&a)[16], cpx<R> (&b)[16], cpx<R>* buf_a,
                                                 cpx<R>* buf_b, int t, const cpx<R>* __restrict__ stw,
                                                 bool inv) {
@@ -363,7 +383,7 @@ __device__ __forceinline__ void block_fft2_regs(cpx<R> (&a)[16], cpx<R> (&b)[16]
       b[m].y = -b[m].y;
     }
   }
-  fft2_stages_regs<R, LOG2N, 0>(a, b, buf_a, buf_b, t, stw);
+  fft2_stages_regs<R, LOG2N, 0, CT>(a, b, buf_a, buf_b, t, stw);
   if (inv) {
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -384,6 +404,66 @@ __device__ __forceinline__ void block_fft2_regs(cpx<R> (&a)[16], cpx<R> (&b)[16]
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+// Asynchronous bulk copies from shared to global memory (the tensor memory
+// accelerator's untiled form): both addresses 16-byte aligned, size a multiple
+// of 16 bytes.  Writes to the source by ordinary stores must be made visible
+// to the copy engine first (fence_proxy_async, then a barrier).  Completion is
+// tracked per issuing thread: bulk_wait_read() returns once the thread's
+// committed copies have read their shared-memory source (it may then be
+// overwritten), bulk_wait_all() once their global writes are done.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, unsigned bytes) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(ssrc));
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst), "r"(s), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
+// Bulk copies from global to shared memory completing on an mbarrier (one
+// arrival with the expected byte count per phase), and a wait on a phase
+// bounded by wall time (%globaltimer): false after `ns` nanoseconds.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_addr(sdst)),
+               "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned long long ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > ns) return false;
+  return true;
+}
 
 // Cooperative copy of `n` table entries from global to shared memory.
 template <typename T>

@@ -17,6 +17,7 @@ namespace dsnu {
 // m_kx and status only.
 struct PlanTables {
   void* stw_x;    // cpx, FFT stage twiddles of length nx (fft_stage_tw_elems)
+  void* stwc_x;   // cpx, the same in compact form (fft_stage_tw_elems_ct)
   void* twm_lo_x; // cpx, e^{-2 pi i n/Mx}, n < Lx = min(64, nx)
   void* twm_hi_x; // cpx, e^{-2 pi i Lx j/Mx}, j < nx/Lx
   void* decon_x;  // real, nx  phi_hat(0)/phi_hat(2 pi (n - nx/2)/Mx)

@@ -57,6 +57,15 @@
 #ifndef DSNU_COL_PAIRED
 #define DSNU_COL_PAIRED 1
 #endif
+// Inverse row pass: Phi rows written by bulk copies from shared memory
+// (measured slower than direct 16-byte stores at 4096^2, so off)
+// Forward row pass: bulk prefetch of the next rows of rho (FP32 plans)
+#ifndef DSNU_ROWF_PF
+#define DSNU_ROWF_PF 1
+#endif
+#ifndef DSNU_ROWI_BULK
+#define DSNU_ROWI_BULK 0
+#endif
 #ifndef DSNU_COL_REGPF
 #define DSNU_COL_REGPF 1
 #endif
@@ -76,6 +85,7 @@ struct AxisTabs {
   const cpx<R>* twm_hi;  // e^{-2 pi i L j/M}, j < N/L
   int log2lo;            // log2 L
   const R* decon;        // phi_hat(0) / phi_hat(2 pi (n - N/2)/M), n < N
+  const cpx<R>* stwc;    // compact stage twiddles (fft_stage_tw_elems_ct); x axis only
 };
 
 // e^{-2 pi i n/M} for n < N from the two short tables (one complex product).
@@ -199,7 +209,20 @@ struct Geo {
   static constexpr int STWP = (STW + 1) & ~1;  // keep the buffers 16-byte aligned
   // FP32 row passes keep e^{-2 pi i n/M} (n < N) in a shared table after the buffers
   static constexpr bool ROW_TAB = sizeof(R) == 4;
-  static constexpr size_t smem_row_fwd = size_t(STWP + 2 * RB_F * RS + (ROW_TAB ? N : 0)) * sizeof(cpx<R>);
+  // FP32 forward row pass: the next item's RB_F rows of rho (FP64) are
+  // prefetched by a bulk copy into a landing buffer while the current item is
+  // transformed; room for it comes from the compact stage table and a half
+  // e^{-2 pi i n/M} table (n < N/2; the rest is -i times it).  Used when the
+  // CTAs per SM that the registers allow still fit in shared memory.
+  static constexpr int STWC = fft_stage_tw_elems_ct(LOG2N) > 0 ? fft_stage_tw_elems_ct(LOG2N) : 1;
+  static constexpr int STWCP = (STWC + 1) & ~1;
+  static constexpr size_t smem_row_fwd_pf =
+      size_t(STWCP + 2 * RB_F * RS + N / 2 + RB_F * N * 8 / int(sizeof(cpx<R>)) + 2) * sizeof(cpx<R>);
+  static constexpr int MINB_F0 = (T_RF >= 512) ? 1 : DSNU_ROW_MINB;
+  static constexpr bool ROW_PF =
+      sizeof(R) == 4 && DSNU_ROWF_PF && MINB_F0 * (smem_row_fwd_pf + 1024) <= size_t(233472);
+  static constexpr size_t smem_row_fwd =
+      ROW_PF ? smem_row_fwd_pf : size_t(STWP + 2 * RB_F * RS + (ROW_TAB ? N : 0)) * sizeof(cpx<R>);
   static constexpr size_t smem_row_inv = size_t(STWP + 2 * RB_I * RS + (ROW_TAB ? N : 0)) * sizeof(cpx<R>);
   // two rows of 512 threads: their threads interleave lane by lane, so that
   // the two rows' elements of a 32-byte row tile are touched by adjacent lanes
@@ -227,16 +250,22 @@ struct Geo {
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_RF, min_blocks<R>(Geo<R, LOG2N>::MINB_F))
 k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
-          const R* __restrict__ decon_y, int cj) {
+          const R* __restrict__ decon_y, int cj, int* status) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, RB = GG::RB_F, T = GG::T_RF, RS = GG::RS;
+  constexpr bool PF = GG::ROW_PF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
-  cpx<R>* sm = stw + GG::STWP;
-  cpx<R>* wtab = sm + 2 * RB * RS;  // e^{-2 pi i n/M}, n < N (FP32)
-  copy_to_smem(stw, ax.stw, GG::STW);
+  cpx<R>* sm = stw + (PF ? GG::STWCP : GG::STWP);
+  cpx<R>* wtab = sm + 2 * RB * RS;  // e^{-2 pi i n/M}: n < N/2 (PF) or n < N (FP32)
+  double* land = reinterpret_cast<double*>(wtab + N / 2);  // PF: the item's RB rows of rho
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(land + RB * N);
+  if constexpr (PF) copy_to_smem(stw, ax.stwc, GG::STWC);
+  else copy_to_smem(stw, ax.stw, GG::STW);
   if constexpr (GG::ROW_TAB)
-    for (int i = threadIdx.x; i < N; i += T) wtab[i] = twm(ax, i);
+    for (int i = threadIdx.x; i < (PF ? N / 2 : N); i += T) wtab[i] = twm(ax, i);
+  if constexpr (PF)
+    if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
   grid_dep_wait();
   const int tid = threadIdx.x;
@@ -246,9 +275,21 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   cpx<R>* buf_e = sm + (2 * rr) * RS;
   cpx<R>* buf_o = buf_e + RS;
   const int items = (ny + RB - 1) / RB;
+  const int total = items * mem.count;
+  // thread 0: the rows of item it2 (contiguous in rho) into the landing buffer
+  auto prefetch = [&](int it2) {
+    const int mi2 = it2 / items;
+    const int r0 = (it2 - mi2 * items) * RB;
+    const unsigned bytes = unsigned(min(RB, ny - r0)) * unsigned(N * sizeof(double));
+    mbar_expect_tx(bar, bytes);
+    bulk_load(land, member_at(mem, mi2).rho + size_t(r0) * N, bytes, bar);
+  };
+  if constexpr (PF)
+    if (tid == 0 && int(blockIdx.x) < total) prefetch(blockIdx.x);
+  unsigned phase = 0;
 #pragma unroll 1
-  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
-    if (it + int(gridDim.x) >= items * mem.count) grid_dep_trigger();  // last item of this CTA
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    if (it + int(gridDim.x) >= total) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     const Member mb = member_at(mem, mi);
     const double* __restrict__ rho = mb.rho;
@@ -258,20 +299,38 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     const int row = row0 + rr;
     const bool valid = row < ny;
     const R dy = valid ? decon_y[row] : R(0);
+    if constexpr (PF) {
+      // bounded wait (1 s): on expiry the status word records it and the
+      // item runs on whatever the buffer holds
+      if (!mbar_wait(bar, phase, 1000000000ull)) atomicExch(status, int(DSNU_ETIMEOUT));
+      phase ^= 1u;
+    }
     cpx<R> e[16], o[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int n = t + G * m;
-      const R x = valid ? from_f64<R>(rho[size_t(row) * N + n]) : R(0);
+      R x;
+      if constexpr (PF) x = valid ? from_f64<R>(land[rr * N + n]) : R(0);
+      else x = valid ? from_f64<R>(rho[size_t(row) * N + n]) : R(0);
       const cpx<R> z = mk<R>(x, isg * (x * ax.decon[n] * dy));
       cpx<R> w;
-      if constexpr (GG::ROW_TAB) w = wtab[n];
-      else w = twm(ax, n);
+      if constexpr (PF) {
+        w = wtab[t + G * (m & 7)];           // n - N/2 for m >= 8, and
+        if (m >= 8) w = mk<R>(w.y, -w.x);   // e^{-2 pi i (n' + N/2)/M} = -i e^{-2 pi i n'/M}
+      } else if constexpr (GG::ROW_TAB) {
+        w = wtab[n];
+      } else {
+        w = twm(ax, n);
+      }
       w.y *= isg;
       e[m] = z;
       o[m] = cmul(z, w);
     }
-    block_fft2_regs<R, LOG2N>(e, o, buf_e, buf_o, t, stw, cj != 0);
+    if constexpr (PF) {
+      __syncthreads();  // every thread has read the landing buffer
+      if (tid == 0 && it + int(gridDim.x) < total) prefetch(it + gridDim.x);
+    }
+    block_fft2_regs<R, LOG2N, PF>(e, o, buf_e, buf_o, t, stw, cj != 0);
     __syncthreads();  // last-stage loads (and the previous unpack) finished
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -780,6 +839,7 @@ k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs
 //   T(2j+1) = IDFT_N[(W(q) - W(q + N)) e^{+2 pi i q/M}](j),   q < N,
 // with W(q) = Y(q) + i S(q) for q <= N and W(M - q) = conj Y(q) + i conj S(q).
 // Both transforms run together; j < N/2 gives the grid points n < N.
+// Phi must be 16-byte aligned (checked on the host).
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(Geo<R, LOG2N>::MINB_I))
 k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
@@ -809,7 +869,6 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     const Member mb = member_at(mem, mi);
     const cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(mb, off.A);
     const cpx<R>* __restrict__ St = ws_ptr<cpx<R>>(mb, off.B);
-    double* __restrict__ phi = mb.phi;
     const int row0 = item * RB;
     const int row = row0 + rr;
     const bool valid = row < ny;
@@ -859,7 +918,20 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
       const cpx<R> d = wlo - whi;
       b[m] = cj ? cmul(d, w) : cmulc(d, w);
     }
+#if DSNU_ROWI_BULK
+    // the previous item's bulk stores have read buf_v (their staging) before
+    // the first stage below overwrites it
+    if (tid < RB) bulk_wait_read();
+#endif
     block_fft2_regs<R, LOG2N>(a, b, buf_u, buf_v, t, stw, cj == 0);
+#if DSNU_ROWI_BULK
+    // Phi's row is staged in this row's buf_v (free after the last stage, at
+    // least N doubles) and written by one bulk copy per row, which runs while
+    // the CTA loads and transforms its next rows
+    double2* stage = reinterpret_cast<double2*>(buf_v);
+#else
+    double* __restrict__ phi = mb.phi;
+#endif
     if (valid) {
       // slot m holds T(2 (t + G m)) in a and T(2 (t + G m) + 1) in b; n < N for m < 8
 #pragma unroll
@@ -870,10 +942,29 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
         double2 out;
         out.x = to_f64<R>((a[m].x + ia * ax.decon[n] * dy) * scale);
         out.y = to_f64<R>((b[m].x + ib * ax.decon[n + 1] * dy) * scale);
+#if DSNU_ROWI_BULK
+        stage[t + G * m] = out;
+#else
         *reinterpret_cast<double2*>(phi + size_t(row) * N + n) = out;
+#endif
       }
     }
+#if DSNU_ROWI_BULK
+    fence_proxy_async();
+    __syncthreads();
+    if (tid < RB) {  // (indices recomputed here: nothing extra stays live across the transforms)
+      const int mi2 = it / items;
+      const int rw = (it - mi2 * items) * RB + tid;
+      if (rw < ny) {
+        bulk_store(member_at(mem, mi2).phi + size_t(rw) * N, sm + (2 * tid + 1) * RS, unsigned(N * sizeof(double)));
+        bulk_commit();
+      }
+    }
+#endif
   }
+#if DSNU_ROWI_BULK
+  if (threadIdx.x < RB) bulk_wait_all();
+#endif
 }
 
 }  // namespace dsnu

@@ -72,6 +72,10 @@ dsnu_status dsnu_solve_noalloc(dsnu_plan plan, const double* rho, double* phi, v
     dsnu::set_last_error("NULL input or output");
     return DSNU_EINVAL;
   }
+  if ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(phi)) & 15) {
+    dsnu::set_last_error("input and output must be 16-byte aligned");
+    return DSNU_EINVAL;
+  }
   const size_t need = plan->ws_layout.total;
   if (need > kStaticScratchBytes) {
     dsnu::set_last_error("dsnu_solve_noalloc: this plan needs " + std::to_string(need) +

@@ -193,9 +193,11 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
   if (g.standard) return run_standard<R>(g, t, L, mem, st, cj, ev);
   const WsOff off{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial};
   const AxisTabs<R> ax{static_cast<const cpx<R>*>(t.stw_x), static_cast<const cpx<R>*>(t.twm_lo_x),
-                       static_cast<const cpx<R>*>(t.twm_hi_x), g.log2lo_x, static_cast<const R*>(t.decon_x)};
+                       static_cast<const cpx<R>*>(t.twm_hi_x), g.log2lo_x, static_cast<const R*>(t.decon_x),
+                       static_cast<const cpx<R>*>(t.stwc_x)};
   const AxisTabs<R> ay{static_cast<const cpx<R>*>(t.stw_y), static_cast<const cpx<R>*>(t.twm_lo_y),
-                       static_cast<const cpx<R>*>(t.twm_hi_y), g.log2lo_y, static_cast<const R*>(t.decon_y)};
+                       static_cast<const cpx<R>*>(t.twm_hi_y), g.log2lo_y, static_cast<const R*>(t.decon_y),
+                       nullptr};
   const MultTabs<R> mt{static_cast<const R*>(t.m_wx2), static_cast<const R*>(t.m_gx),
                        g.n_gy, R(1.0 / (g.sigma * g.sigma)),
                        R(-g.dky2 / (g.sigma * g.sigma) * 1.4426950408889634), R(g.dky2), g.ny, g.sharp,
@@ -209,7 +211,8 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
 #define DSNU_ROWF(L2)                                                                               \
   launch_k(g.pdl != 0, k_row_fwd<R, L2>,                                                            \
            dim3(persistent_grid(nm * ((g.ny + Geo<R, L2>::RB_F - 1) / Geo<R, L2>::RB_F), g.cap_rowf)), \
-           dim3(Geo<R, L2>::T_RF), Geo<R, L2>::smem_row_fwd, st, mem, off, ldqA, ldqB, g.Q, g.ny, ax, dcy, cj)
+           dim3(Geo<R, L2>::T_RF), Geo<R, L2>::smem_row_fwd, st, mem, off, ldqA, ldqB, g.Q, g.ny, ax, dcy, cj, \
+           t.status)
 #define DSNU_COLM(L2)                                                                               \
   if (g.m_generic)                                                                                  \
     launch_k(g.pdl != 0, k_col_main<R, L2, true>,                                                   \

@@ -196,7 +196,7 @@ struct EsFourier {
 template <typename R>
 struct HostTables {
   // complex tables interleaved (re, im)
-  std::vector<R> stw_x, twm_lo_x, twm_hi_x, decon_x, stw_y, twm_lo_y, twm_hi_y, decon_y;
+  std::vector<R> stw_x, stwc_x, twm_lo_x, twm_hi_x, decon_x, stw_y, twm_lo_y, twm_hi_y, decon_y;
   std::vector<R> m_wx2, m_gx, m_gy, m_kx;
   std::vector<int2> node_q0;
   std::vector<R> node_w;
@@ -289,6 +289,28 @@ static void fft_stage_twiddles(int log2n, std::vector<double>& out) {
       }
   }
   if (out.empty()) out.assign(2, 0.0);
+}
+
+// The compact form (fft_stage_tw_elems_ct): stage 1 as above, then the two
+// factor tables of the stage with NS = 256 (N >= 512).
+static void fft_stage_twiddles_ct(int log2n, std::vector<double>& out) {
+  if (log2n <= 8) {
+    fft_stage_twiddles(log2n, out);
+    return;
+  }
+  out.clear();
+  auto put = [&](double a) {
+    out.push_back(std::cos(a));
+    out.push_back(std::sin(a));
+  };
+  for (int r = 1; r < 16; ++r)
+    for (int k = 0; k < 16; ++k) put(-2.0 * M_PI * double(r) * double(k) / 256.0);
+  const int rad = 1 << (log2n - 8);
+  const double span = 256.0 * double(rad);
+  for (int r = 1; r < rad; ++r)
+    for (int k1 = 0; k1 < 16; ++k1) put(-2.0 * M_PI * double(r) * double(16 * k1) / span);
+  for (int r = 1; r < rad; ++r)
+    for (int k0 = 0; k0 < 16; ++k0) put(-2.0 * M_PI * double(r) * double(k0) / span);
 }
 
 // e^{-2 pi i n/M}, n < N, as a product of two short tables:
@@ -467,8 +489,10 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   std::vector<double> tmp, tmp2;
   fft_stage_twiddles(g.log2nx, tmp); T.stw_x = cast<R>(tmp);
   fft_stage_twiddles(g.log2ny, tmp); T.stw_y = cast<R>(tmp);
+  fft_stage_twiddles_ct(g.log2nx, tmp); T.stwc_x = cast<R>(tmp);
   if (int(T.stw_x.size()) != 2 * std::max(1, fft_stage_tw_elems(g.log2nx)) ||
-      int(T.stw_y.size()) != 2 * std::max(1, fft_stage_tw_elems(g.log2ny)))
+      int(T.stw_y.size()) != 2 * std::max(1, fft_stage_tw_elems(g.log2ny)) ||
+      int(T.stwc_x.size()) != 2 * std::max(1, fft_stage_tw_elems_ct(g.log2nx)))
     return fail(DSNU_EINVAL, "internal: stage twiddle table size mismatch");
   g.log2lo_x = half_angle_tables(nx, tmp, tmp2); T.twm_lo_x = cast<R>(tmp); T.twm_hi_x = cast<R>(tmp2);
   g.log2lo_y = half_angle_tables(ny, tmp, tmp2); T.twm_lo_y = cast<R>(tmp); T.twm_hi_y = cast<R>(tmp2);
@@ -528,7 +552,7 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   // one device block for every table
   Builder b;
   const size_t o_stx = b.add(T.stw_x), o_tlx = b.add(T.twm_lo_x), o_thx = b.add(T.twm_hi_x);
-  const size_t o_dx = b.add(T.decon_x);
+  const size_t o_dx = b.add(T.decon_x), o_scx = b.add(T.stwc_x);
   const size_t o_sty = b.add(T.stw_y), o_tly = b.add(T.twm_lo_y), o_thy = b.add(T.twm_hi_y);
   const size_t o_dy = b.add(T.decon_y);
   const size_t o_wx2 = b.add(T.m_wx2), o_gx = b.add(T.m_gx), o_gy = b.add(T.m_gy), o_kx = b.add(T.m_kx);
@@ -547,6 +571,7 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   char* d = static_cast<char*>(dev);
   PlanTables& t = P->tab;
   t.stw_x = d + o_stx; t.twm_lo_x = d + o_tlx; t.twm_hi_x = d + o_thx; t.decon_x = d + o_dx;
+  t.stwc_x = d + o_scx;
   t.stw_y = d + o_sty; t.twm_lo_y = d + o_tly; t.twm_hi_y = d + o_thy; t.decon_y = d + o_dy;
   t.m_wx2 = d + o_wx2; t.m_gx = d + o_gx; t.m_gy = d + o_gy; t.m_kx = d + o_kx;
   t.node_q0 = reinterpret_cast<int2*>(d + o_q0);
@@ -771,6 +796,8 @@ dsnu_status dsnu_set_workspace(dsnu_plan plan, void* ws, size_t bytes) {
 static dsnu_status run(dsnu_plan plan, const double* in, double* out, void* stream, int cj) {
   if (!plan) return fail(DSNU_EINVAL, "NULL plan");
   if (!in || !out) return fail(DSNU_EINVAL, "NULL input or output");
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15)
+    return fail(DSNU_EINVAL, "input and output must be 16-byte aligned");
   if (!plan->ws) return fail(DSNU_EINVAL, "no workspace attached (dsnu_set_workspace)");
   const size_t nbytes = size_t(plan->geom.nx) * plan->geom.ny * sizeof(double);
   const char* a = reinterpret_cast<const char*>(in);
@@ -846,6 +873,9 @@ dsnu_status dsnu_solve_host(dsnu_plan plan, const double* rho_host, double* phi_
                             double* phi_dev, void* stream) {
   if (!plan) return fail(DSNU_EINVAL, "NULL plan");
   if (!rho_host || !phi_host || !rho_dev || !phi_dev) return fail(DSNU_EINVAL, "NULL buffer");
+  if ((reinterpret_cast<uintptr_t>(rho_dev) | reinterpret_cast<uintptr_t>(phi_dev)) & 15)
+    return fail(DSNU_EINVAL, "device buffers must be 16-byte aligned");
+  if (!plan->ws) return fail(DSNU_EINVAL, "no workspace attached (dsnu_set_workspace)");
   const size_t nbytes = size_t(plan->geom.nx) * plan->geom.ny * sizeof(double);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(rho_dev, rho_host, nbytes, cudaMemcpyHostToDevice, st);

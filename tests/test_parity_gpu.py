@@ -253,3 +253,34 @@ def test_solve_host_stream_matches_device_solves():
     torch.cuda.synchronize()
     assert torch.equal(last, plan.solve(rhos[1].cuda()).cpu())
     plan.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_misaligned_buffers_are_rejected_before_any_launch(prec):
+    """rho and phi must be 16-byte aligned (the kernels move 16-byte vectors
+    and bulk copies): an 8-byte-aligned view is refused with DSNU_EINVAL on
+    every entry point, nothing is launched, and the plan keeps working."""
+    from paper_1409_2014_gb300 import Batch, Plan, _abi
+
+    n = 64
+    plan = Plan(n, lx=8.0, cut_radius=4.0, n_r=16, n_theta=64, precision=prec)
+    store = torch.zeros(n * n + 1, dtype=torch.float64, device="cuda")
+    odd = store[1:].view(n, n)  # contiguous, data pointer 8 bytes past a 16-byte boundary
+    good = torch.from_numpy(synth.density_sum(n, n, 8.0, 8.0, seed=5, count=3)).cuda()
+    out = torch.empty_like(good)
+    for call in (lambda: plan.solve(odd, out), lambda: plan.solve(good, odd),
+                 lambda: plan.solve_adjoint(odd, out),
+                 lambda: plan.solve_host(good.cpu(), out.cpu(), odd, out),
+                 lambda: _abi.dsnu_solve_noalloc(plan.handle, good.data_ptr(), odd.data_ptr(),
+                                                 torch.cuda.current_stream().cuda_stream)):
+        with pytest.raises(_abi.DsnuError) as ei:
+            call()
+        assert ei.value.status == _abi.DSNU_EINVAL
+        assert "16-byte" in _abi.dsnu_last_error()
+    with pytest.raises(_abi.DsnuError):
+        Batch([plan], [good], [odd])
+    torch.cuda.synchronize()
+    assert float(odd.abs().max()) == 0.0  # nothing was written
+    ref = plan.solve(good)
+    assert torch.isfinite(ref).all() and float(ref.abs().max()) > 0
+    plan.close()
