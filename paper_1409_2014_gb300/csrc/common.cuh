@@ -465,6 +465,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   return true;
 }
 
+// Per-thread asynchronous 16-byte copies global -> shared (through L2 only);
+// cp_async_wait_all() returns once this thread's copies have landed (a
+// barrier then makes them visible to the block).
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Cooperative copy of `n` table entries from global to shared memory.
 template <typename T>
 __device__ __forceinline__ void copy_to_smem(T* __restrict__ dst, const T* __restrict__ src, int n) {

@@ -63,6 +63,10 @@
 #ifndef DSNU_ROWF_PF
 #define DSNU_ROWF_PF 1
 #endif
+// Inverse row pass: asynchronous prefetch of the next row pair of A (FP32)
+#ifndef DSNU_ROWI_PF
+#define DSNU_ROWI_PF 1
+#endif
 #ifndef DSNU_ROWI_BULK
 #define DSNU_ROWI_BULK 0
 #endif
@@ -223,7 +227,16 @@ struct Geo {
       sizeof(R) == 4 && DSNU_ROWF_PF && MINB_F0 * (smem_row_fwd_pf + 1024) <= size_t(233472);
   static constexpr size_t smem_row_fwd =
       ROW_PF ? smem_row_fwd_pf : size_t(STWP + 2 * RB_F * RS + (ROW_TAB ? N : 0)) * sizeof(cpx<R>);
-  static constexpr size_t smem_row_inv = size_t(STWP + 2 * RB_I * RS + (ROW_TAB ? N : 0)) * sizeof(cpx<R>);
+  // FP32 inverse row pass with two rows per CTA: the next row pair of A
+  // ((N + 1) 16-byte segments of the row tiles) is prefetched by per-thread
+  // asynchronous copies into a landing buffer [q][2], with the same compact
+  // stage table and half twiddle table as the forward pass.
+  static constexpr size_t smem_row_inv_pf = size_t(STWCP + 2 * RB_I * RS + N / 2 + 2 * (N + 1)) * sizeof(cpx<R>);
+  static constexpr int MINB_I0 = (T_RI >= 512) ? 1 : DSNU_ROW_MINB;
+  static constexpr bool ROWI_PF = sizeof(R) == 4 && DSNU_ROWI_PF && RB_I == 2 && TR == 4 &&
+                                  MINB_I0 * (smem_row_inv_pf + 1024) <= size_t(233472);
+  static constexpr size_t smem_row_inv =
+      ROWI_PF ? smem_row_inv_pf : size_t(STWP + 2 * RB_I * RS + (ROW_TAB ? N : 0)) * sizeof(cpx<R>);
   // two rows of 512 threads: their threads interleave lane by lane, so that
   // the two rows' elements of a 32-byte row tile are touched by adjacent lanes
   static constexpr bool ILV_F = (RB_F == 2);
@@ -845,14 +858,17 @@ __global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(Geo<R, LOG2
 k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
           const R* __restrict__ decon_y, R scale, int cj) {
   using GG = Geo<R, LOG2N>;
-  constexpr int N = GG::N, G = GG::G, RB = GG::RB_I, RS = GG::RS;
+  constexpr int N = GG::N, G = GG::G, RB = GG::RB_I, RS = GG::RS, T = GG::T_RI;
+  constexpr bool PF = GG::ROWI_PF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
-  cpx<R>* sm = stw + GG::STWP;
-  cpx<R>* wtab = sm + 2 * RB * RS;  // e^{-2 pi i q/M}, q < N (FP32)
-  copy_to_smem(stw, ax.stw, GG::STW);
+  cpx<R>* sm = stw + (PF ? GG::STWCP : GG::STWP);
+  cpx<R>* wtab = sm + 2 * RB * RS;  // e^{-2 pi i q/M}: q < N/2 (PF) or q < N (FP32)
+  cpx<R>* land = wtab + N / 2;      // PF: Y(q) of the item's two rows at [2 q + row], q <= N
+  if constexpr (PF) copy_to_smem(stw, ax.stwc, GG::STWC);
+  else copy_to_smem(stw, ax.stw, GG::STW);
   if constexpr (GG::ROW_TAB)
-    for (int i = threadIdx.x; i < N; i += GG::T_RI) wtab[i] = twm(ax, i);
+    for (int i = threadIdx.x; i < (PF ? N / 2 : N); i += T) wtab[i] = twm(ax, i);
   __syncthreads();
   grid_dep_wait();
   const int tid = threadIdx.x;
@@ -862,9 +878,21 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   cpx<R>* buf_u = sm + (2 * rr) * RS;
   cpx<R>* buf_v = buf_u + RS;
   const int items = (ny + RB - 1) / RB;
+  const int total = items * mem.count;
+  // every thread: its share of the (N + 1) 16-byte segments (both rows at one
+  // q) of item it2's row pair
+  auto prefetch = [&](int it2) {
+    const int mi2 = it2 / items;
+    const cpx<R>* src = ws_ptr<cpx<R>>(member_at(mem, mi2), off.A) +
+                        Tile<R>::at((it2 - mi2 * items) * RB, 0, ldqA);
+    for (int q = tid; q <= N; q += T) cp_async16(land + 2 * q, src + size_t(q) * Tile<R>::TR);
+    cp_async_commit();
+  };
+  if constexpr (PF)
+    if (int(blockIdx.x) < total) prefetch(blockIdx.x);
 #pragma unroll 1
-  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
-    if (it + int(gridDim.x) >= items * mem.count) grid_dep_trigger();  // last item of this CTA
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    if (it + int(gridDim.x) >= total) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     const Member mb = member_at(mem, mi);
     const cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(mb, off.A);
@@ -876,54 +904,95 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     // U(q) = W(q) + W(q + N) and V(q) = (W(q) - W(q + N)) e^{+2 pi i q/M} for
     // the q = t + G m this thread owns in the first FFT stage, formed in
     // registers.  W(q + N) is W(N) for q = 0 and built from the conjugates at
-    // the mirror N - q otherwise.  Each Y(q), q < N, is loaded once (all loads
-    // of the row are issued together) and its mirror is taken from the other
-    // thread through shared memory; the few band values S are loaded directly.
+    // the mirror N - q otherwise.  Without the prefetch each Y(q), q < N, is
+    // loaded once (all loads of the row are issued together) and its mirror is
+    // taken from the other thread through shared memory; with it both come
+    // from the landing buffer.  The few band values S are loaded directly.
     const cpx<R> z = mk<R>(R(0), R(0));
-    cpx<R> y[16], s[16], sm2[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int q = t + G * m;
-      const int qm = (q == 0) ? N : N - q;
-      y[m] = valid ? A[Tile<R>::at(row, q, ldqA)] : z;
-      s[m] = (valid && q <= Q) ? St[Tile<R>::at(row, q, ldqB)] : z;
-      sm2[m] = (valid && qm <= Q) ? St[Tile<R>::at(row, qm, ldqB)] : z;
-    }
-    const cpx<R> yN = (valid && t == 0) ? A[Tile<R>::at(row, N, ldqA)] : z;
-    __syncthreads();  // the previous transform's last-stage loads of buf_u are done
-#pragma unroll
-    for (int m = 0; m < 16; ++m) buf_u[pad16(t + G * m)] = y[m];
-    __syncthreads();
-    cpx<R> ym[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int q = t + G * m;
-      ym[m] = (q == 0) ? yN : buf_u[pad16(N - q)];
-    }
     cpx<R> a[16], b[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) {
-      const int q = t + G * m;
-      cpx<R> yh = ym[m], sh = sm2[m];
-      if (q != 0) {
-        yh = conj(yh);
-        sh = conj(sh);
+    // e^{-2 pi i q/M} for q = t + G m (the inverse uses its conjugate)
+    auto twq = [&](int m) {
+      cpx<R> w;
+      if constexpr (PF) {
+        w = wtab[t + G * (m & 7)];
+        if (m >= 8) w = mk<R>(w.y, -w.x);  // -i e^{-2 pi i (q - N/2)/M}
+      } else if constexpr (GG::ROW_TAB) {
+        w = wtab[t + G * m];
+      } else {
+        w = twm(ax, t + G * m);
       }
-      const cpx<R> wlo = y[m] + mul_i(s[m], si);
-      const cpx<R> whi = yh + mul_i(sh, si);
-      a[m] = wlo + whi;
-      cpx<R> w;  // e^{-2 pi i q/M}; the inverse uses its conjugate
-      if constexpr (GG::ROW_TAB) w = wtab[q];
-      else w = twm(ax, q);
-      const cpx<R> d = wlo - whi;
-      b[m] = cj ? cmul(d, w) : cmulc(d, w);
+      return w;
+    };
+    if constexpr (PF) {
+      cpx<R> s[16], sm2[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int q = t + G * m;
+        const int qm = (q == 0) ? N : N - q;
+        s[m] = (valid && q <= Q) ? St[Tile<R>::at(row, q, ldqB)] : z;
+        sm2[m] = (valid && qm <= Q) ? St[Tile<R>::at(row, qm, ldqB)] : z;
+      }
+      cp_async_wait_all();
+      __syncthreads();  // the row pair has landed; the previous transform's last-stage loads are done
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int q = t + G * m;
+        const cpx<R> y = land[2 * q + rr];
+        cpx<R> yh = land[2 * ((q == 0) ? N : N - q) + rr], sh = sm2[m];
+        if (q != 0) {
+          yh = conj(yh);
+          sh = conj(sh);
+        }
+        const cpx<R> wlo = y + mul_i(s[m], si);
+        const cpx<R> whi = yh + mul_i(sh, si);
+        a[m] = wlo + whi;
+        const cpx<R> d = wlo - whi, w = twq(m);
+        b[m] = cj ? cmul(d, w) : cmulc(d, w);
+      }
+      __syncthreads();  // every thread has read the landing buffer
+      if (it + int(gridDim.x) < total) prefetch(it + gridDim.x);
+    } else {
+      cpx<R> y[16], s[16], sm2[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int q = t + G * m;
+        const int qm = (q == 0) ? N : N - q;
+        y[m] = valid ? A[Tile<R>::at(row, q, ldqA)] : z;
+        s[m] = (valid && q <= Q) ? St[Tile<R>::at(row, q, ldqB)] : z;
+        sm2[m] = (valid && qm <= Q) ? St[Tile<R>::at(row, qm, ldqB)] : z;
+      }
+      const cpx<R> yN = (valid && t == 0) ? A[Tile<R>::at(row, N, ldqA)] : z;
+      __syncthreads();  // the previous transform's last-stage loads of buf_u are done
+#pragma unroll
+      for (int m = 0; m < 16; ++m) buf_u[pad16(t + G * m)] = y[m];
+      __syncthreads();
+      cpx<R> ym[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int q = t + G * m;
+        ym[m] = (q == 0) ? yN : buf_u[pad16(N - q)];
+      }
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int q = t + G * m;
+        cpx<R> yh = ym[m], sh = sm2[m];
+        if (q != 0) {
+          yh = conj(yh);
+          sh = conj(sh);
+        }
+        const cpx<R> wlo = y[m] + mul_i(s[m], si);
+        const cpx<R> whi = yh + mul_i(sh, si);
+        a[m] = wlo + whi;
+        const cpx<R> d = wlo - whi, w = twq(m);
+        b[m] = cj ? cmul(d, w) : cmulc(d, w);
+      }
     }
 #if DSNU_ROWI_BULK
     // the previous item's bulk stores have read buf_v (their staging) before
     // the first stage below overwrites it
     if (tid < RB) bulk_wait_read();
 #endif
-    block_fft2_regs<R, LOG2N>(a, b, buf_u, buf_v, t, stw, cj == 0);
+    block_fft2_regs<R, LOG2N, PF>(a, b, buf_u, buf_v, t, stw, cj == 0);
 #if DSNU_ROWI_BULK
     // Phi's row is staged in this row's buf_v (free after the last stage, at
     // least N doubles) and written by one bulk copy per row, which runs while
