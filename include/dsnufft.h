@@ -384,6 +384,10 @@ typedef struct {
   int32_t spread_tile;   /* spreading configuration chosen at plan creation: */
   int32_t spread_split;  /*   tile edge (cells), threads per cell, entries per item */
   int32_t spread_chunk;
+  int32_t row_prefetch;  /* FP32 row passes: bit 0 the forward pass prefetches rho,
+                            bit 1 the inverse pass prefetches its spectra, bit 2 also
+                            its band values (by grid size and what fits in shared memory) */
+  int32_t reserved;
 } dsnu_plan_info;
 
 dsnu_status dsnu_plan_get_info(dsnu_plan plan, dsnu_plan_info* info);

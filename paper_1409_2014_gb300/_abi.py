@@ -61,6 +61,7 @@ class dsnu_plan_info(ctypes.Structure):
         ("n_tiles", ctypes.c_int32), ("max_tile_nodes", ctypes.c_int32),
         ("n_items", ctypes.c_int32), ("spread_tile", ctypes.c_int32),
         ("spread_split", ctypes.c_int32), ("spread_chunk", ctypes.c_int32),
+        ("row_prefetch", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 

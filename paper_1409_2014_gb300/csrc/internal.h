@@ -70,6 +70,9 @@ struct PlanGeom {
   int n_gy;                // entries of the short partition table
   double dky2;             // dk_y^2
   int cap_rowf, cap_col, cap_bandf, cap_bandi, cap_rowi;  // resident CTAs (SMs x occupancy)
+  int rowi_bpf;            // inverse row pass prefetches the band values too (FP32)
+  int row_pf;              // bit 0 forward row prefetch, bit 1 inverse, bit 2 rowi_bpf
+  size_t smem_rowi;        // its dynamic shared memory per CTA
   int w, Q, n_nodes, n_tiles, tiles_x, tiles_y, max_tile_nodes, n_items;
   int spread_cfg;          // index into kSpreadCfgs (chosen by the autotuner)
   int spread_tile;         // its tile edge (cells)

@@ -63,6 +63,12 @@
 #ifndef DSNU_ROWF_PF
 #define DSNU_ROWF_PF 1
 #endif
+#ifndef DSNU_ROWF_LPAD
+#define DSNU_ROWF_LPAD 8
+#endif
+#ifndef DSNU_ROWI_BPF
+#define DSNU_ROWI_BPF 1
+#endif
 // Inverse row pass: asynchronous prefetch of the next row pair of A (FP32)
 #ifndef DSNU_ROWI_PF
 #define DSNU_ROWI_PF 1
@@ -220,8 +226,11 @@ struct Geo {
   // CTAs per SM that the registers allow still fit in shared memory.
   static constexpr int STWC = fft_stage_tw_elems_ct(LOG2N) > 0 ? fft_stage_tw_elems_ct(LOG2N) : 1;
   static constexpr int STWCP = (STWC + 1) & ~1;
+  // (landing rows N + 8 doubles apart, so that the two rows read by one
+  // half-warp fall in different banks)
+  static constexpr int LS = N + DSNU_ROWF_LPAD;
   static constexpr size_t smem_row_fwd_pf =
-      size_t(STWCP + 2 * RB_F * RS + N / 2 + RB_F * N * 8 / int(sizeof(cpx<R>)) + 2) * sizeof(cpx<R>);
+      size_t(STWCP + 2 * RB_F * RS + N / 2 + RB_F * LS * 8 / int(sizeof(cpx<R>)) + 2) * sizeof(cpx<R>);
   static constexpr int MINB_F0 = (T_RF >= 512) ? 1 : DSNU_ROW_MINB;
   static constexpr bool ROW_PF =
       sizeof(R) == 4 && DSNU_ROWF_PF && MINB_F0 * (smem_row_fwd_pf + 1024) <= size_t(233472);
@@ -237,6 +246,10 @@ struct Geo {
                                   MINB_I0 * (smem_row_inv_pf + 1024) <= size_t(233472);
   static constexpr size_t smem_row_inv =
       ROWI_PF ? smem_row_inv_pf : size_t(STWP + 2 * RB_I * RS + (ROW_TAB ? N : 0)) * sizeof(cpx<R>);
+  // with the prefetch, the band values S(q), q <= Q, of the row pair can be
+  // prefetched too, into 16 (Q + 1) more bytes after the landing buffer (the
+  // launch then asks for them; the kernel's limit is set to the maximum)
+  static constexpr size_t smem_row_inv_limit = ROWI_PF ? size_t(232448) : smem_row_inv;
   // two rows of 512 threads: their threads interleave lane by lane, so that
   // the two rows' elements of a 32-byte row tile are touched by adjacent lanes
   static constexpr bool ILV_F = (RB_F == 2);
@@ -271,8 +284,8 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* sm = stw + (PF ? GG::STWCP : GG::STWP);
   cpx<R>* wtab = sm + 2 * RB * RS;  // e^{-2 pi i n/M}: n < N/2 (PF) or n < N (FP32)
-  double* land = reinterpret_cast<double*>(wtab + N / 2);  // PF: the item's RB rows of rho
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(land + RB * N);
+  double* land = reinterpret_cast<double*>(wtab + N / 2);  // PF: the item's RB rows of rho, LS apart
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(land + RB * GG::LS);
   if constexpr (PF) copy_to_smem(stw, ax.stwc, GG::STWC);
   else copy_to_smem(stw, ax.stw, GG::STW);
   if constexpr (GG::ROW_TAB)
@@ -289,13 +302,14 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   cpx<R>* buf_o = buf_e + RS;
   const int items = (ny + RB - 1) / RB;
   const int total = items * mem.count;
-  // thread 0: the rows of item it2 (contiguous in rho) into the landing buffer
+  // thread 0: the rows of item it2 into the landing buffer, one copy per row
   auto prefetch = [&](int it2) {
     const int mi2 = it2 / items;
     const int r0 = (it2 - mi2 * items) * RB;
-    const unsigned bytes = unsigned(min(RB, ny - r0)) * unsigned(N * sizeof(double));
-    mbar_expect_tx(bar, bytes);
-    bulk_load(land, member_at(mem, mi2).rho + size_t(r0) * N, bytes, bar);
+    const int nr = min(RB, ny - r0);
+    const double* src = member_at(mem, mi2).rho + size_t(r0) * N;
+    mbar_expect_tx(bar, unsigned(nr) * unsigned(N * sizeof(double)));
+    for (int r = 0; r < nr; ++r) bulk_load(land + r * GG::LS, src + size_t(r) * N, unsigned(N * sizeof(double)), bar);
   };
   if constexpr (PF)
     if (tid == 0 && int(blockIdx.x) < total) prefetch(blockIdx.x);
@@ -323,7 +337,7 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     for (int m = 0; m < 16; ++m) {
       const int n = t + G * m;
       R x;
-      if constexpr (PF) x = valid ? from_f64<R>(land[rr * N + n]) : R(0);
+      if constexpr (PF) x = valid ? from_f64<R>(land[rr * GG::LS + n]) : R(0);
       else x = valid ? from_f64<R>(rho[size_t(row) * N + n]) : R(0);
       const cpx<R> z = mk<R>(x, isg * (x * ax.decon[n] * dy));
       cpx<R> w;
@@ -856,7 +870,7 @@ k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(Geo<R, LOG2N>::MINB_I))
 k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
-          const R* __restrict__ decon_y, R scale, int cj) {
+          const R* __restrict__ decon_y, R scale, int cj, int bpf) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, RB = GG::RB_I, RS = GG::RS, T = GG::T_RI;
   constexpr bool PF = GG::ROWI_PF;
@@ -865,6 +879,7 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   cpx<R>* sm = stw + (PF ? GG::STWCP : GG::STWP);
   cpx<R>* wtab = sm + 2 * RB * RS;  // e^{-2 pi i q/M}: q < N/2 (PF) or q < N (FP32)
   cpx<R>* land = wtab + N / 2;      // PF: Y(q) of the item's two rows at [2 q + row], q <= N
+  cpx<R>* land_s = land + 2 * (N + 1);  // PF and bpf: S(q) likewise, q <= Q
   if constexpr (PF) copy_to_smem(stw, ax.stwc, GG::STWC);
   else copy_to_smem(stw, ax.stw, GG::STW);
   if constexpr (GG::ROW_TAB)
@@ -886,6 +901,11 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     const cpx<R>* src = ws_ptr<cpx<R>>(member_at(mem, mi2), off.A) +
                         Tile<R>::at((it2 - mi2 * items) * RB, 0, ldqA);
     for (int q = tid; q <= N; q += T) cp_async16(land + 2 * q, src + size_t(q) * Tile<R>::TR);
+    if (bpf) {
+      const cpx<R>* srs = ws_ptr<cpx<R>>(member_at(mem, mi2), off.B) +
+                          Tile<R>::at((it2 - mi2 * items) * RB, 0, ldqB);
+      for (int q = tid; q <= Q; q += T) cp_async16(land_s + 2 * q, srs + size_t(q) * Tile<R>::TR);
+    }
     cp_async_commit();
   };
   if constexpr (PF)
@@ -924,26 +944,23 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
       return w;
     };
     if constexpr (PF) {
-      cpx<R> s[16], sm2[16];
-#pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        const int q = t + G * m;
-        const int qm = (q == 0) ? N : N - q;
-        s[m] = (valid && q <= Q) ? St[Tile<R>::at(row, q, ldqB)] : z;
-        sm2[m] = (valid && qm <= Q) ? St[Tile<R>::at(row, qm, ldqB)] : z;
-      }
       cp_async_wait_all();
       __syncthreads();  // the row pair has landed; the previous transform's last-stage loads are done
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int q = t + G * m;
+        const int qm = (q == 0) ? N : N - q;
+        // band values: prefetched (bpf) or loaded here
+        cpx<R> sv = z, sh = z;
+        if (q <= Q) sv = bpf ? land_s[2 * q + rr] : St[Tile<R>::at(row, q, ldqB)];
+        if (qm <= Q) sh = bpf ? land_s[2 * qm + rr] : St[Tile<R>::at(row, qm, ldqB)];
         const cpx<R> y = land[2 * q + rr];
-        cpx<R> yh = land[2 * ((q == 0) ? N : N - q) + rr], sh = sm2[m];
+        cpx<R> yh = land[2 * qm + rr];
         if (q != 0) {
           yh = conj(yh);
           sh = conj(sh);
         }
-        const cpx<R> wlo = y + mul_i(s[m], si);
+        const cpx<R> wlo = y + mul_i(sv, si);
         const cpx<R> whi = yh + mul_i(sh, si);
         a[m] = wlo + whi;
         const cpx<R> d = wlo - whi, w = twq(m);

@@ -45,9 +45,21 @@ cudaError_t prepare_rows(PlanGeom& g) {
   if ((e = cudaFuncSetAttribute(k_row_fwd<R, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(GG::smem_row_fwd)))) return e;
   if ((e = cudaFuncSetAttribute(k_row_inv<R, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(GG::smem_row_inv)))) return e;
+                                int(GG::smem_row_inv_limit)))) return e;
+  // the band values of the inverse row pass are prefetched when they fit
+  // without lowering the CTAs per SM
+  g.rowi_bpf = 0;
+  g.smem_rowi = GG::smem_row_inv;
+  if constexpr (GG::ROWI_PF && DSNU_ROWI_BPF) {
+    const size_t with_s = GG::smem_row_inv + size_t(16) * size_t(g.Q + 1);
+    if (with_s <= GG::smem_row_inv_limit && size_t(GG::MINB_I0) * (with_s + 1024) <= size_t(233472)) {
+      g.rowi_bpf = 1;
+      g.smem_rowi = with_s;
+    }
+  }
+  g.row_pf = (GG::ROW_PF ? 1 : 0) | (GG::ROWI_PF ? 2 : 0) | (g.rowi_bpf ? 4 : 0);
   if ((e = resident_ctas(k_row_fwd<R, L2>, GG::T_RF, GG::smem_row_fwd, &g.cap_rowf))) return e;
-  return resident_ctas(k_row_inv<R, L2>, GG::T_RI, GG::smem_row_inv, &g.cap_rowi);
+  return resident_ctas(k_row_inv<R, L2>, GG::T_RI, g.smem_rowi, &g.cap_rowi);
 }
 
 template <typename R, int L2>
@@ -233,8 +245,8 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
 #define DSNU_ROWI(L2)                                                                               \
   launch_k(g.pdl != 0, k_row_inv<R, L2>,                                                            \
            dim3(persistent_grid(nm * ((g.ny + Geo<R, L2>::RB_I - 1) / Geo<R, L2>::RB_I), g.cap_rowi)), \
-           dim3(Geo<R, L2>::T_RI), Geo<R, L2>::smem_row_inv, st, mem, off, ldqA, ldqB, g.Q, g.ny, ax, dcy, \
-           R(g.scale), cj)
+           dim3(Geo<R, L2>::T_RI), g.smem_rowi, st, mem, off, ldqA, ldqB, g.Q, g.ny, ax, dcy, R(g.scale), cj, \
+           g.rowi_bpf)
 #define DSNU_MARK(I) \
   if (ev) cudaEventRecord(ev[I], st)
   // the band chain (type-2 columns, interpolation, weighting, spreading,

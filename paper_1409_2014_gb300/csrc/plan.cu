@@ -1066,6 +1066,8 @@ dsnu_status dsnu_plan_get_info(dsnu_plan plan, dsnu_plan_info* info) {
   info->spread_tile = g.spread_tile;
   info->spread_split = kSpreadCfgs[g.spread_cfg].split;
   info->spread_chunk = kSpreadCfgs[g.spread_cfg].chunk;
+  info->row_prefetch = g.standard ? 0 : g.row_pf;
+  info->reserved = 0;
   return DSNU_OK;
 }
 

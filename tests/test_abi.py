@@ -47,7 +47,7 @@ def test_struct_layout_matches_header(tmp_path):
     assert _abi.dsnu_params.n_r.offset == 40
     assert _abi.dsnu_params.partition.offset == 60
     assert _abi.dsnu_params.radial_rule.offset == 64
-    assert ctypes.sizeof(_abi.dsnu_plan_info) == 56
+    assert ctypes.sizeof(_abi.dsnu_plan_info) == 64
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")

@@ -284,3 +284,33 @@ def test_misaligned_buffers_are_rejected_before_any_launch(prec):
     ref = plan.solve(good)
     assert torch.isfinite(ref).all() and float(ref.abs().max()) > 0
     plan.close()
+
+
+# 2048^2 and 4096^2 mixed plans run the row passes with their prefetching
+# forms; the inverse pass also prefetches the band values when 16 (Q + 1)
+# bytes fit in shared memory.  Each path is compared with the oracle on a
+# stride-16 sample of the grid (4096 polar nodes keep the oracle's direct
+# sums to seconds).
+LARGE = [
+    # n, L, P, expected row_prefetch bits
+    (2048, 16.0, 6.0, 7),   # Q = 65: band values prefetched
+    (2048, 32.0, 8.0, 3),   # Q = 167: band values loaded directly
+    (4096, 64.0, 8.0, 7),   # the benchmark's grid and disk, Q = 329
+    (4096, 64.0, 12.0, 3),  # Q = 493
+]
+
+
+@pytest.mark.parametrize("n,L,P,bits", LARGE)
+def test_large_grids_prefetch_paths_vs_oracle(n, L, P, bits):
+    from paper_1409_2014_gb300 import Plan
+
+    rho = synth.density_abs2(n, n, L, L, seed=n + int(P), count=12)
+    plan = Plan(n, lx=L, cut_radius=P, n_r=32, n_theta=128, precision="mixed")
+    assert plan.info.row_prefetch == bits, plan.info.band_q
+    got = plan.solve(torch.from_numpy(rho).cuda()).cpu().numpy()
+    plan.close()
+    rows = np.arange(3, n, 16)
+    cols = np.arange(5, n, 16)
+    op = oracle.OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=P, n_r=32, n_theta=128)
+    ref = oracle.solve(rho, op, rows=rows, cols=cols)
+    assert rel_linf(got[np.ix_(rows, cols)], ref) <= TOL["mixed"]
