@@ -405,27 +405,10 @@ __device__ __forceinline__ void block_fft2_regs(cpx<R> (&a)[16], cpx<R> (&b)[16]
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
-// Asynchronous bulk copies from shared to global memory (the tensor memory
-// accelerator's untiled form): both addresses 16-byte aligned, size a multiple
-// of 16 bytes.  Writes to the source by ordinary stores must be made visible
-// to the copy engine first (fence_proxy_async, then a barrier).  Completion is
-// tracked per issuing thread: bulk_wait_read() returns once the thread's
-// committed copies have read their shared-memory source (it may then be
-// overwritten), bulk_wait_all() once their global writes are done.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, unsigned bytes) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(ssrc));
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst), "r"(s), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
-
 // Bulk copies from global to shared memory completing on an mbarrier (one
-// arrival with the expected byte count per phase), and a wait on a phase
-// bounded by wall time (%globaltimer): false after `ns` nanoseconds.
+// arrival with the expected byte count per phase) under an L2 eviction-priority
+// policy, and a wait on a phase bounded by wall time (%globaltimer): false
+// after `ns` nanoseconds.
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
@@ -437,11 +420,19 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, unsigned bytes, unsigned long long* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                   smem_addr(sdst)),
-               "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
+// L2 eviction priority "evict first" for data read once
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, unsigned bytes, unsigned long long* bar,
+                                          unsigned long long pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;\n" ::
+          "r"(smem_addr(sdst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+      : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
   unsigned done;

@@ -73,9 +73,6 @@
 #ifndef DSNU_ROWI_PF
 #define DSNU_ROWI_PF 1
 #endif
-#ifndef DSNU_ROWI_BULK
-#define DSNU_ROWI_BULK 0
-#endif
 #ifndef DSNU_COL_REGPF
 #define DSNU_COL_REGPF 1
 #endif
@@ -309,7 +306,10 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     const int nr = min(RB, ny - r0);
     const double* src = member_at(mem, mi2).rho + size_t(r0) * N;
     mbar_expect_tx(bar, unsigned(nr) * unsigned(N * sizeof(double)));
-    for (int r = 0; r < nr; ++r) bulk_load(land + r * GG::LS, src + size_t(r) * N, unsigned(N * sizeof(double)), bar);
+    // rho is read once: its lines go first when L2 needs room (keeps more of A and B resident)
+    const unsigned long long pol = l2_evict_first();
+    for (int r = 0; r < nr; ++r)
+      bulk_load(land + r * GG::LS, src + size_t(r) * N, unsigned(N * sizeof(double)), bar, pol);
   };
   if constexpr (PF)
     if (tid == 0 && int(blockIdx.x) < total) prefetch(blockIdx.x);
@@ -1004,20 +1004,8 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
         b[m] = cj ? cmul(d, w) : cmulc(d, w);
       }
     }
-#if DSNU_ROWI_BULK
-    // the previous item's bulk stores have read buf_v (their staging) before
-    // the first stage below overwrites it
-    if (tid < RB) bulk_wait_read();
-#endif
     block_fft2_regs<R, LOG2N, PF>(a, b, buf_u, buf_v, t, stw, cj == 0);
-#if DSNU_ROWI_BULK
-    // Phi's row is staged in this row's buf_v (free after the last stage, at
-    // least N doubles) and written by one bulk copy per row, which runs while
-    // the CTA loads and transforms its next rows
-    double2* stage = reinterpret_cast<double2*>(buf_v);
-#else
     double* __restrict__ phi = mb.phi;
-#endif
     if (valid) {
       // slot m holds T(2 (t + G m)) in a and T(2 (t + G m) + 1) in b; n < N for m < 8
 #pragma unroll
@@ -1028,29 +1016,10 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
         double2 out;
         out.x = to_f64<R>((a[m].x + ia * ax.decon[n] * dy) * scale);
         out.y = to_f64<R>((b[m].x + ib * ax.decon[n + 1] * dy) * scale);
-#if DSNU_ROWI_BULK
-        stage[t + G * m] = out;
-#else
         *reinterpret_cast<double2*>(phi + size_t(row) * N + n) = out;
-#endif
       }
     }
-#if DSNU_ROWI_BULK
-    fence_proxy_async();
-    __syncthreads();
-    if (tid < RB) {  // (indices recomputed here: nothing extra stays live across the transforms)
-      const int mi2 = it / items;
-      const int rw = (it - mi2 * items) * RB + tid;
-      if (rw < ny) {
-        bulk_store(member_at(mem, mi2).phi + size_t(rw) * N, sm + (2 * tid + 1) * RS, unsigned(N * sizeof(double)));
-        bulk_commit();
-      }
-    }
-#endif
   }
-#if DSNU_ROWI_BULK
-  if (threadIdx.x < RB) bulk_wait_all();
-#endif
 }
 
 }  // namespace dsnu
