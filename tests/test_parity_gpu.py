@@ -302,15 +302,27 @@ LARGE = [
 
 @pytest.mark.parametrize("n,L,P,bits", LARGE)
 def test_large_grids_prefetch_paths_vs_oracle(n, L, P, bits):
+    _large_case(n, n, L, L, P, bits)
+
+
+@pytest.mark.parametrize("nx,ny,lx,ly,P,bits", [
+    (4096, 256, 64.0, 4.0, 6.0, 7),     # long rows, few row pairs; Q = 249 (set by x)
+    (2048, 4096, 32.0, 64.0, 6.0, 3),   # dk_x != dk_y; Q = 249 (set by y) too wide to prefetch at 2048
+])
+def test_rectangular_large_grids_vs_oracle(nx, ny, lx, ly, P, bits):
+    _large_case(nx, ny, lx, ly, P, bits)
+
+
+def _large_case(nx, ny, lx, ly, P, bits):
     from paper_1409_2014_gb300 import Plan
 
-    rho = synth.density_abs2(n, n, L, L, seed=n + int(P), count=12)
-    plan = Plan(n, lx=L, cut_radius=P, n_r=32, n_theta=128, precision="mixed")
+    rho = synth.density_abs2(nx, ny, lx, ly, seed=nx + ny + int(P), count=12)
+    plan = Plan(nx, ny, lx=lx, ly=ly, cut_radius=P, n_r=32, n_theta=128, precision="mixed")
     assert plan.info.row_prefetch == bits, plan.info.band_q
     got = plan.solve(torch.from_numpy(rho).cuda()).cpu().numpy()
     plan.close()
-    rows = np.arange(3, n, 16)
-    cols = np.arange(5, n, 16)
-    op = oracle.OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=P, n_r=32, n_theta=128)
+    rows = np.arange(3, ny, 16)
+    cols = np.arange(5, nx, 16)
+    op = oracle.OracleParams(nx=nx, ny=ny, lx=lx, ly=ly, cut_radius=P, n_r=32, n_theta=128)
     ref = oracle.solve(rho, op, rows=rows, cols=cols)
     assert rel_linf(got[np.ix_(rows, cols)], ref) <= TOL["mixed"]
