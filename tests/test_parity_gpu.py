@@ -319,8 +319,13 @@ def _large_case(nx, ny, lx, ly, P, bits):
     rho = synth.density_abs2(nx, ny, lx, ly, seed=nx + ny + int(P), count=12)
     plan = Plan(nx, ny, lx=lx, ly=ly, cut_radius=P, n_r=32, n_theta=128, precision="mixed")
     assert plan.info.row_prefetch == bits, plan.info.band_q
-    got = plan.solve(torch.from_numpy(rho).cuda()).cpu().numpy()
+    x = torch.from_numpy(rho).cuda()
+    got = plan.solve(x).cpu().numpy()
+    # the conjugated pipeline (the transpose) through the same prefetching
+    # kernels: equal to the solve up to rounding, the operator being symmetric
+    adj = plan.solve_adjoint(x).cpu().numpy()
     plan.close()
+    assert rel_linf(adj, got) <= 2 * TOL["mixed"]
     rows = np.arange(3, ny, 16)
     cols = np.arange(5, nx, 16)
     op = oracle.OracleParams(nx=nx, ny=ny, lx=lx, ly=ly, cut_radius=P, n_r=32, n_theta=128)
