@@ -176,7 +176,7 @@ struct StageInfo {
   static constexpr int tw_off = fft_stage_tw_offset(LOG2N, S);
 };
 
-template <typename R, int LOG2N, int S>
+template <typename R, int LOG2N, int S, bool CT = false>
 __device__ __forceinline__ void fft_stage_regs(cpx<R> (&v)[16], cpx<R>* buf, int t,
                                                const cpx<R>* __restrict__ stw) {
   using SI = StageInfo<LOG2N, S>;
@@ -204,7 +204,12 @@ __device__ __forceinline__ void fft_stage_regs(cpx<R> (&v)[16], cpx<R>* buf, int
   for (int b = 0; b < PER; ++b) {
     const int j = t + b * G;
     const int k = j & (NS - 1);
-    if constexpr (LOG2NS > 0) {
+    if constexpr (CT && LOG2NS == 8) {  // compact table: w = hi[r][k >> 4] lo[r][k & 15]
+      const cpx<R>* hi = stw + 15 * 16 + (k >> 4);
+      const cpx<R>* lo = stw + 15 * 16 + (RAD - 1) * 16 + (k & 15);
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) v[b * RAD + r] = cmul(v[b * RAD + r], cmul(hi[(r - 1) * 16], lo[(r - 1) * 16]));
+    } else if constexpr (LOG2NS > 0) {
       const cpx<R>* tws = stw + SI::tw_off + k;
 #pragma unroll
       for (int r = 1; r < RAD; ++r) v[b * RAD + r] = cmul(v[b * RAD + r], tws[(r - 1) * NS]);
@@ -238,16 +243,17 @@ __device__ __forceinline__ void fft_stage_regs(cpx<R> (&v)[16], cpx<R>* buf, int
   }
 }
 
-template <typename R, int LOG2N, int S>
+template <typename R, int LOG2N, int S, bool CT = false>
 __device__ __forceinline__ void fft_stages_regs(cpx<R> (&v)[16], cpx<R>* buf, int t,
                                                 const cpx<R>* __restrict__ stw) {
   if constexpr (S < StageInfo<LOG2N, 0>::nstages) {
-    fft_stage_regs<R, LOG2N, S>(v, buf, t, stw);
-    fft_stages_regs<R, LOG2N, S + 1>(v, buf, t, stw);
+    fft_stage_regs<R, LOG2N, S, CT>(v, buf, t, stw);
+    fft_stages_regs<R, LOG2N, S + 1, CT>(v, buf, t, stw);
   }
 }
 
-template <typename R, int LOG2N>
+// CT = true: `stw` is the compact stage table (fft_stage_tw_elems_ct).
+template <typename R, int LOG2N, bool CT = false>
 __device__ __forceinline__ void block_fft_regs(cpx<R> (&v)[16], cpx<R>* buf, int t,
                                                const cpx<R>* __restrict__ stw, bool inv) {
   static_assert(LOG2N >= 4 && LOG2N <= 12, "FFT length 16..4096");
@@ -255,7 +261,7 @@ __device__ __forceinline__ void block_fft_regs(cpx<R> (&v)[16], cpx<R>* buf, int
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m].y = -v[m].y;
   }
-  fft_stages_regs<R, LOG2N, 0>(v, buf, t, stw);
+  fft_stages_regs<R, LOG2N, 0, CT>(v, buf, t, stw);
   if (inv) {
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m].y = -v[m].y;

@@ -13,8 +13,8 @@ namespace dsnu {
 
 // Device tables of a plan.  Real-valued tables are in the plan's working
 // precision (float for DSNU_MIXED, double for DSNU_FP64); node_D is FP64.
-// The standard solver uses stw_x, stw_y, m_wx2 ((q_x dk_x)^2, q_x <= nx/2),
-// m_kx and status only.
+// The standard solver uses stw_x, stwc_x, stw_y, m_wx2 ((q_x dk_x)^2,
+// q_x <= nx/2), m_kx and status only.
 struct PlanTables {
   void* stw_x;    // cpx, FFT stage twiddles of length nx (fft_stage_tw_elems)
   void* stwc_x;   // cpx, the same in compact form (fft_stage_tw_elems_ct)

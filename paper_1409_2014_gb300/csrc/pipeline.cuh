@@ -83,10 +83,10 @@ cudaError_t prepare_std_rows(PlanGeom& g) {
   using GS = GeoStd<R, L2>;
   const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_std_row_fwd<R, L2>, A, int(GS::smem)))) return e;
-  if ((e = cudaFuncSetAttribute(k_std_row_inv<R, L2>, A, int(GS::smem)))) return e;
-  if ((e = resident_ctas(k_std_row_fwd<R, L2>, GS::T, GS::smem, &g.cap_rowf))) return e;
-  return resident_ctas(k_std_row_inv<R, L2>, GS::T, GS::smem, &g.cap_rowi);
+  if ((e = cudaFuncSetAttribute(k_std_row_fwd<R, L2>, A, int(GS::smem_rowf)))) return e;
+  if ((e = cudaFuncSetAttribute(k_std_row_inv<R, L2>, A, int(GS::smem_rowi)))) return e;
+  if ((e = resident_ctas(k_std_row_fwd<R, L2>, GS::T, GS::smem_rowf, &g.cap_rowf))) return e;
+  return resident_ctas(k_std_row_inv<R, L2>, GS::T, GS::smem_rowi, &g.cap_rowi);
 }
 
 template <typename R, int L2>
@@ -144,7 +144,8 @@ cudaError_t prepare_kernels(PlanGeom& g) {
 template <typename R>
 dsnu_status run_standard(const PlanGeom& g, const PlanTables& t, const WsLayout& L, const Members& mem,
                          cudaStream_t st, int cj, cudaEvent_t* ev) {
-  const cpx<R>* sx = static_cast<const cpx<R>*>(t.stw_x);
+  // FP32 row passes read the compact stage table (GeoStd::PF)
+  const cpx<R>* sx = static_cast<const cpx<R>*>(sizeof(R) == 4 ? t.stwc_x : t.stw_x);
   const cpx<R>* sy = static_cast<const cpx<R>*>(t.stw_y);
   MultTabs<R> mt{};
   mt.wx2 = static_cast<const R*>(t.m_wx2);
@@ -158,19 +159,20 @@ dsnu_status run_standard(const PlanGeom& g, const PlanTables& t, const WsLayout&
   mt.kx = static_cast<const R*>(t.m_kx);
   const long nm = mem.count;
   const int ldq = L.ldqA;
-#define DSNU_SROWF(L2)                                                                         \
-  k_std_row_fwd<R, L2><<<persistent_grid(nm * ((g.ny / 2 + GeoStd<R, L2>::PER - 1) /            \
-                                               GeoStd<R, L2>::PER), g.cap_rowf),               \
-                         GeoStd<R, L2>::T, GeoStd<R, L2>::smem, st>>>(mem, L.off_A, ldq, g.ny, sx, cj)
-#define DSNU_SCOL(L2)                                                                          \
-  k_std_col<R, L2><<<persistent_grid(nm * ((ldq + GeoStd<R, L2>::PER - 1) / GeoStd<R, L2>::PER), \
-                                     g.cap_col),                                                \
-                     GeoStd<R, L2>::T, GeoStd<R, L2>::smem, st>>>(mem, L.off_A, ldq, ldq, sy, mt,  \
-                                                                  R(g.scale), cj)
-#define DSNU_SROWI(L2)                                                                         \
-  k_std_row_inv<R, L2><<<persistent_grid(nm * ((g.ny / 2 + GeoStd<R, L2>::PER - 1) /            \
-                                               GeoStd<R, L2>::PER), g.cap_rowi),               \
-                         GeoStd<R, L2>::T, GeoStd<R, L2>::smem, st>>>(mem, L.off_A, ldq, g.ny, sx, cj)
+#define DSNU_SROWF(L2)                                                                             \
+  launch_k(g.pdl != 0, k_std_row_fwd<R, L2>,                                                       \
+           dim3(persistent_grid(nm * ((g.ny / 2 + GeoStd<R, L2>::PER - 1) / GeoStd<R, L2>::PER),    \
+                                g.cap_rowf)),                                                      \
+           dim3(GeoStd<R, L2>::T), GeoStd<R, L2>::smem_rowf, st, mem, L.off_A, ldq, g.ny, sx, cj, t.status)
+#define DSNU_SCOL(L2)                                                                              \
+  launch_k(g.pdl != 0, k_std_col<R, L2>,                                                           \
+           dim3(persistent_grid(nm * ((ldq + GeoStd<R, L2>::PER - 1) / GeoStd<R, L2>::PER), g.cap_col)), \
+           dim3(GeoStd<R, L2>::T), GeoStd<R, L2>::smem, st, mem, L.off_A, ldq, ldq, sy, mt, R(g.scale), cj)
+#define DSNU_SROWI(L2)                                                                             \
+  launch_k(g.pdl != 0, k_std_row_inv<R, L2>,                                                       \
+           dim3(persistent_grid(nm * ((g.ny / 2 + GeoStd<R, L2>::PER - 1) / GeoStd<R, L2>::PER),    \
+                                g.cap_rowi)),                                                      \
+           dim3(GeoStd<R, L2>::T), GeoStd<R, L2>::smem_rowi, st, mem, L.off_A, ldq, g.ny, sx, cj)
   if (ev) cudaEventRecord(ev[0], st);
   switch (g.log2nx) {
     DSNU_LOG2_CASES(DSNU_SROWF)

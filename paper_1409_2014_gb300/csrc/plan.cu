@@ -594,6 +594,8 @@ static dsnu_status build_tables_standard(dsnu_plan_s* P, cudaStream_t st) {
   const std::vector<R> stw_x = cast<R>(tmp);
   fft_stage_twiddles(g.log2ny, tmp);
   const std::vector<R> stw_y = cast<R>(tmp);
+  fft_stage_twiddles_ct(g.log2nx, tmp);
+  const std::vector<R> stwc_x = cast<R>(tmp);
   const double dkx = M_PI / p.lx, dky = M_PI / p.ly;
   std::vector<R> wx2(g.nx / 2 + 1), kx(g.nx / 2 + 1);
   for (int q = 0; q <= g.nx / 2; ++q) {
@@ -603,6 +605,7 @@ static dsnu_status build_tables_standard(dsnu_plan_s* P, cudaStream_t st) {
   g.dky2 = dky * dky;
   Builder b;
   const size_t o_stx = b.add(stw_x), o_sty = b.add(stw_y), o_wx2 = b.add(wx2), o_kx = b.add(kx);
+  const size_t o_scx = b.add(stwc_x);
   const int zero = 0;
   const size_t o_st = b.add(&zero, sizeof(int));
   void* dev = nullptr;
@@ -617,6 +620,7 @@ static dsnu_status build_tables_standard(dsnu_plan_s* P, cudaStream_t st) {
   char* d = static_cast<char*>(dev);
   PlanTables& t = P->tab;
   t.stw_x = d + o_stx;
+  t.stwc_x = d + o_scx;
   t.stw_y = d + o_sty;
   t.m_wx2 = d + o_wx2;
   t.m_kx = d + o_kx;

@@ -17,6 +17,14 @@
 //                   imaginary parts of the inverse are the two rows of Phi.
 // `cj` = 1 conjugates every transform (the transposed operator, equal to the
 // operator itself since m is real and even).
+//
+// FP32 plans (PF): the row passes read their inputs from shared-memory
+// landing buffers filled while the previous item is transformed (a bulk copy
+// of the item's rows of rho; cp.async of the row pairs' 16-byte segments of the
+// half spectrum), with the compact stage table making room; the column pass
+// (N >= 512) loads its next column into registers during the current inverse
+// transform.
+// All three are launched with programmatic stream serialization.
 #pragma once
 
 #include "kernels.cuh"
@@ -33,38 +41,83 @@ struct GeoStd {
   static constexpr int STW = fft_stage_tw_elems(LOG2N) > 0 ? fft_stage_tw_elems(LOG2N) : 1;
   static constexpr int STWP = (STW + 1) & ~1;
   static constexpr size_t smem = size_t(STWP + PER * FB) * sizeof(cpx<R>);
+  static constexpr bool PF = sizeof(R) == 4;
+  static constexpr int STWC = fft_stage_tw_elems_ct(LOG2N) > 0 ? fft_stage_tw_elems_ct(LOG2N) : 1;
+  static constexpr int STWCP = (STWC + 1) & ~1;
+  // forward rows: 2 PER rows of rho (FP64) and an mbarrier after the buffers
+  static constexpr size_t smem_rowf =
+      PF ? size_t(STWCP + PER * FB) * sizeof(cpx<R>) + size_t(2 * PER) * N * sizeof(double) + 16 : smem;
+  // inverse rows: PER row pairs x (N/2 + 1) segments of 16 bytes
+  static constexpr size_t smem_rowi =
+      PF ? size_t(STWCP + PER * FB) * sizeof(cpx<R>) + size_t(PER) * (N / 2 + 1) * 16 : smem;
 };
 
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(GeoStd<R, LOG2N>::T, min_blocks<R>(2))
-k_std_row_fwd(Members mem, size_t offH, int ldq, int ny, const cpx<R>* __restrict__ stw_g, int cj) {
+k_std_row_fwd(Members mem, size_t offH, int ldq, int ny, const cpx<R>* __restrict__ stw_g, int cj, int* status) {
   using GG = GeoStd<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, PER = GG::PER;
+  constexpr bool PF = GG::PF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
-  copy_to_smem(stw, stw_g, GG::STW);
+  copy_to_smem(stw, stw_g, PF ? GG::STWC : GG::STW);
   const int tid = threadIdx.x;
   const int rr = tid / G, t = tid - rr * G;
-  cpx<R>* buf = stw + GG::STWP + rr * GG::FB;
+  cpx<R>* buf = stw + (PF ? GG::STWCP : GG::STWP) + rr * GG::FB;
+  double* land = reinterpret_cast<double*>(stw + (PF ? GG::STWCP : GG::STWP) + PER * GG::FB);  // PF: 2 PER rows
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(land + 2 * PER * N);
+  if constexpr (PF)
+    if (tid == 0) mbar_init(bar, 1);
+  __syncthreads();
+  grid_dep_wait();
   const int pairs = ny / 2;
   const int items = (pairs + PER - 1) / PER;
+  const int total = items * mem.count;
+  // thread 0: the 2 PER rows of item it2 (contiguous in rho) in one bulk copy
+  auto prefetch = [&](int it2) {
+    const int mi2 = it2 / items;
+    const int r0 = 2 * (it2 - mi2 * items) * PER;
+    const unsigned bytes = unsigned(min(2 * PER, ny - r0)) * unsigned(N * sizeof(double));
+    mbar_expect_tx(bar, bytes);
+    bulk_load(land, member_at(mem, mi2).rho + size_t(r0) * N, bytes, bar, l2_evict_first());
+  };
+  if constexpr (PF)
+    if (tid == 0 && int(blockIdx.x) < total) prefetch(blockIdx.x);
+  unsigned phase = 0;
 #pragma unroll 1
-  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    if (it + int(gridDim.x) >= total) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     const Member mb = member_at(mem, mi);
     cpx<R>* __restrict__ H = ws_ptr<cpx<R>>(mb, offH);
     const int pr = item * PER + rr;
     const bool valid = pr < pairs;
     const int row = 2 * pr;
+    if constexpr (PF) {
+      if (!mbar_wait(bar, phase, 1000000000ull)) atomicExch(status, int(DSNU_ETIMEOUT));
+      phase ^= 1u;
+    }
     cpx<R> v[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int n = t + G * m;
-      const R a = valid ? from_f64<R>(mb.rho[size_t(row) * N + n]) : R(0);
-      const R b = valid ? from_f64<R>(mb.rho[size_t(row + 1) * N + n]) : R(0);
+      R a = R(0), b = R(0);
+      if (valid) {
+        if constexpr (PF) {
+          a = from_f64<R>(land[(2 * rr) * N + n]);
+          b = from_f64<R>(land[(2 * rr + 1) * N + n]);
+        } else {
+          a = from_f64<R>(mb.rho[size_t(row) * N + n]);
+          b = from_f64<R>(mb.rho[size_t(row + 1) * N + n]);
+        }
+      }
       v[m] = mk<R>(a, b);
     }
-    block_fft_regs<R, LOG2N>(v, buf, t, stw, cj != 0);
+    if constexpr (PF) {
+      __syncthreads();  // every thread has read the landing buffer
+      if (tid == 0 && it + int(gridDim.x) < total) prefetch(it + gridDim.x);
+    }
+    block_fft_regs<R, LOG2N, PF>(v, buf, t, stw, cj != 0);
     __syncthreads();  // the last stage's loads of buf are done
 #pragma unroll
     for (int m = 0; m < 16; ++m) buf[pad16(t + G * m)] = v[m];
@@ -77,8 +130,12 @@ k_std_row_fwd(Members mem, size_t offH, int ldq, int ny, const cpx<R>* __restric
         const cpx<R> xa = mk<R>(R(0.5) * (zq.x + zm.x), R(0.5) * (zq.y - zm.y));
         const cpx<R> xb = mk<R>(R(0.5) * (zq.y + zm.y), R(-0.5) * (zq.x - zm.x));
         cpx<R>* dst = H + Tile<R>::at(row, q, ldq);  // row + 1 is the next element
-        dst[0] = xa;
-        dst[1] = xb;
+        if constexpr (sizeof(R) == 4) {              // (16-byte aligned: row is even)
+          *reinterpret_cast<float4*>(dst) = make_float4(xa.x, xa.y, xb.x, xb.y);
+        } else {
+          dst[0] = xa;
+          dst[1] = xb;
+        }
       }
     }
   }
@@ -90,15 +147,33 @@ k_std_col(Members mem, size_t offH, int ldq, int ncols, const cpx<R>* __restrict
           MultTabs<R> mt, R scale, int cj) {
   using GG = GeoStd<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, PER = GG::PER;
+  constexpr bool PF = GG::PF && LOG2N >= 9;  // (below, the registers for it are not there)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
   copy_to_smem(stw, stw_g, GG::STW);
   const int tid = threadIdx.x;
   const int cl = tid / G, t = tid - cl * G;
   cpx<R>* buf = stw + GG::STWP + cl * GG::FB;
+  __syncthreads();
+  grid_dep_wait();
   const int items = (ncols + PER - 1) / PER;
+  const int total = items * mem.count;
+  // PF: the next column's values are loaded into registers before the
+  // current column's inverse transform
+  cpx<R> xn[PF ? 16 : 1];
+  auto load_col = [&](int it2) {
+    const int mi2 = it2 / items;
+    const int col2 = (it2 - mi2 * items) * PER + cl;
+    const cpx<R>* H2 = ws_ptr<cpx<R>>(member_at(mem, mi2), offH);
+#pragma unroll
+    for (int m = 0; m < (PF ? 16 : 1); ++m)
+      xn[m] = (col2 < ncols) ? H2[Tile<R>::at(t + G * m, col2, ldq)] : mk<R>(R(0), R(0));
+  };
+  if constexpr (PF)
+    if (int(blockIdx.x) < total) load_col(blockIdx.x);
 #pragma unroll 1
-  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    if (it + int(gridDim.x) >= total) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     cpx<R>* __restrict__ H = ws_ptr<cpx<R>>(member_at(mem, mi), offH);
     const int col = item * PER + cl;
@@ -107,7 +182,10 @@ k_std_col(Members mem, size_t offH, int ldq, int ncols, const cpx<R>* __restrict
     const R kxc = (valid && mt.generic) ? mt.kx[col] : R(0);
     cpx<R> v[16];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = valid ? H[Tile<R>::at(t + G * m, col, ldq)] : mk<R>(R(0), R(0));
+    for (int m = 0; m < 16; ++m) {
+      if constexpr (PF) v[m] = xn[m];
+      else v[m] = valid ? H[Tile<R>::at(t + G * m, col, ldq)] : mk<R>(R(0), R(0));
+    }
     block_fft_regs<R, LOG2N>(v, buf, t, stw, cj != 0);
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -122,6 +200,8 @@ k_std_col(Members mem, size_t offH, int ldq, int ncols, const cpx<R>* __restrict
         mlt = (s == R(0)) ? R(0) : -fdiv(kx2, s) * scale;
       v[m] = v[m] * mlt;
     }
+    if constexpr (PF)
+      if (it + int(gridDim.x) < total) load_col(it + gridDim.x);
     block_fft_regs<R, LOG2N>(v, buf, t, stw, cj == 0);
     if (valid) {
 #pragma unroll
@@ -134,23 +214,48 @@ template <typename R, int LOG2N>
 __global__ void __launch_bounds__(GeoStd<R, LOG2N>::T, min_blocks<R>(2))
 k_std_row_inv(Members mem, size_t offH, int ldq, int ny, const cpx<R>* __restrict__ stw_g, int cj) {
   using GG = GeoStd<R, LOG2N>;
-  constexpr int N = GG::N, G = GG::G, PER = GG::PER;
+  constexpr int N = GG::N, G = GG::G, PER = GG::PER, T = GG::T;
+  constexpr bool PF = GG::PF;
+  constexpr int HS = N / 2 + 1;  // segments per row pair
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
-  copy_to_smem(stw, stw_g, GG::STW);
+  copy_to_smem(stw, stw_g, PF ? GG::STWC : GG::STW);
   const int tid = threadIdx.x;
   const int rr = tid / G, t = tid - rr * G;
-  cpx<R>* buf = stw + GG::STWP + rr * GG::FB;
+  cpx<R>* buf = stw + (PF ? GG::STWCP : GG::STWP) + rr * GG::FB;
+  // PF: Y_a(q), Y_b(q) of each row pair of the item at [2 (pair HS + q) + row]
+  cpx<R>* land = stw + (PF ? GG::STWCP : GG::STWP) + PER * GG::FB;
+  __syncthreads();
+  grid_dep_wait();
   const int pairs = ny / 2;
   const int items = (pairs + PER - 1) / PER;
+  const int total = items * mem.count;
+  // every thread: its share of the item's PER x (N/2 + 1) 16-byte segments
+  auto prefetch = [&](int it2) {
+    const int mi2 = it2 / items;
+    const int p0 = (it2 - mi2 * items) * PER;
+    const cpx<R>* H2 = ws_ptr<cpx<R>>(member_at(mem, mi2), offH);
+    for (int i = tid; i < PER * HS; i += T) {
+      const int p = i / HS, q = i - p * HS;
+      if (p0 + p < pairs) cp_async16(land + 2 * i, H2 + Tile<R>::at(2 * (p0 + p), q, ldq));
+    }
+    cp_async_commit();
+  };
+  if constexpr (PF)
+    if (int(blockIdx.x) < total) prefetch(blockIdx.x);
 #pragma unroll 1
-  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    if (it + int(gridDim.x) >= total) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     const Member mb = member_at(mem, mi);
     const cpx<R>* __restrict__ H = ws_ptr<cpx<R>>(mb, offH);
     const int pr = item * PER + rr;
     const bool valid = pr < pairs;
     const int row = 2 * pr;
+    if constexpr (PF) {
+      cp_async_wait_all();
+      __syncthreads();  // the item's segments have landed
+    }
     cpx<R> v[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -159,7 +264,7 @@ k_std_row_inv(Members mem, size_t offH, int ldq, int ny, const cpx<R>* __restric
       const int qq = hi ? N - q : q;
       cpx<R> ya = mk<R>(R(0), R(0)), yb = ya;
       if (valid) {
-        const cpx<R>* src = H + Tile<R>::at(row, qq, ldq);
+        const cpx<R>* src = PF ? land + 2 * (rr * HS + qq) : H + Tile<R>::at(row, qq, ldq);
         ya = src[0];
         yb = src[1];
       }
@@ -169,7 +274,11 @@ k_std_row_inv(Members mem, size_t offH, int ldq, int ny, const cpx<R>* __restric
       }
       v[m] = mk<R>(ya.x - yb.y, ya.y + yb.x);  // Y_a + i Y_b
     }
-    block_fft_regs<R, LOG2N>(v, buf, t, stw, cj == 0);
+    if constexpr (PF) {
+      __syncthreads();  // every thread has read the landing buffer
+      if (it + int(gridDim.x) < total) prefetch(it + gridDim.x);
+    }
+    block_fft_regs<R, LOG2N, PF>(v, buf, t, stw, cj == 0);
     if (valid) {
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
