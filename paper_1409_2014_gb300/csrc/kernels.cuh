@@ -419,12 +419,15 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
   cpx<R>* buf_e = sm + (2 * cl) * FB;
   cpx<R>* buf_o = buf_e + FB;
   cpx<R>* wtab = sm + 2 * CC * FB;                       // N entries (TAB only)
-  float2* mtab = reinterpret_cast<float2*>(wtab + N);    // N + 1 entries (TAB only)
+  // N + 1 entries (TAB only), even a first then odd a: a warp reads a's of
+  // one parity (a = |qbar| of the rows 2 (t + G m) + h), so consecutive entries
+  float2* mtab = reinterpret_cast<float2*>(wtab + N);
+  constexpr int MH = N / 2 + 1;  // even entries
   if constexpr (TAB) {
     for (int i = tid; i < N; i += GG::T_C) wtab[i] = twm(ay, i);
     for (int i = tid; i <= N; i += GG::T_C) {
       const R a2 = R(i * i);
-      mtab[i] = make_float2(a2 * mt.dky2, exp2f(a2 * mt.neg_dky2_s2_log2e));
+      mtab[(i & 1) ? MH + (i >> 1) : (i >> 1)] = make_float2(a2 * mt.dky2, exp2f(a2 * mt.neg_dky2_s2_log2e));
     }
     __syncthreads();
   }
@@ -479,7 +482,7 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
         for (int h = 0; h < 2; ++h) {
           const int qq = q + h;
           const int a = (qq < N) ? qq : 2 * N - qq;
-          const float2 tv = mtab[a];
+          const float2 tv = mtab[(h ? MH : 0) + (a >> 1)];  // a has the parity of qq
           const R s = wx2 + tv.x;
           const R part = mt.sharp ? ((s > mt.cut2) ? R(1) : R(0)) : (R(1) - (R(1) - gx) * tv.y);
           const R mv = (s == R(0) || !valid) ? R(0) : -fdiv(wx2, (s == R(0)) ? R(1) : s) * part;
