@@ -167,7 +167,7 @@ def algorithmic_bytes(stage: str, n: int, Q: int, csz: int, n_nodes: int, w: int
     nodes = n_nodes * (8 + 2 * w * rsz + 8 + csz)  # q0, weights, D, c
     return float({
         "row_fwd": 8 * n * n + A + Bc,
-        "col_main": 2 * A,
+        "col_main": 2 * A + (n + 1) * (n + 4) * 4 * (csz == 8),  # FP32: + the multiplier table rows
         "band_fwd": Bc + band,
         "interp": band + nodes,
         "spread": nodes + n_items * tile * tile * csz,     # node data in, one partial tile per item out

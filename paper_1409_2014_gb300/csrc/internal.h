@@ -39,6 +39,8 @@ struct PlanTables {
   int2* ent_q0;   // per entry: stencil origin of the node
   void* ent_w;    // real, per entry: the node's 2w ES weights
   int* status;    // one int
+  float* m1tab;   // FP32 split plans with the DS multiplier: m1(q_x, |qbar_y|), (nx + 1) rows of ny + 4
+                  // floats, each row's even |qbar_y| first (see MultTabs::m1); else NULL
 };
 
 
@@ -140,6 +142,7 @@ struct dsnu_plan_s {
   dsnu::WsLayout ws_layout;
   void* table_block;        // one device allocation holding every table but the spreading ones
   void* spread_block;       // spreading tables of the chosen tile configuration
+  void* m1_block;           // PlanTables::m1tab
   size_t table_bytes;
   void* ws;                 // caller-owned workspace
   size_t ws_bytes;

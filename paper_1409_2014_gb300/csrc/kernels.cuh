@@ -118,6 +118,12 @@ struct MultTabs {
   R a0, ac, as2;      // as2 = 2 as
   R dky;              // dk_y
   const R* kx;        // k_x of column q_x for the sin 2theta term (0 at the Nyquist column)
+  // FP32 plans with the DS multiplier: m1(q_x, a) for a = |qbar_y| <= N_y,
+  // computed in FP64 at plan creation, one row of ldm floats per column with
+  // the even a first (a = 2 j at j) and the odd a after them (a = 2 j' + 1 at
+  // N_y/2 + 1 + j')
+  const float* m1;
+  int ldm;
 };
 
 // The angular and radial factor of the generic multiplier at (k_x, qbar_y):
@@ -257,7 +263,10 @@ struct Geo {
   // FP32 column pass of I1 with the DS multiplier: two shared tables on top,
   // e^{-2 pi i n/M} (n < N) and {(a dk_y)^2, e^{-(a dk_y)^2/sigma^2}} (a <= N)
   static constexpr bool COL_TAB = sizeof(R) == 4;
-  static constexpr size_t smem_col_main = smem_col + (COL_TAB ? size_t(N) * 8 + size_t(N + 1) * 8 : 0);
+  // and two buffers of CC multiplier rows (N + 4 floats each), the current
+  // item's and the next one's
+  static constexpr int LDM = N + 4;
+  static constexpr size_t smem_col_main = smem_col + (COL_TAB ? size_t(N) * 8 + size_t(2 * CC * LDM) * 4 : 0);
   static_assert(LOG2N >= 4 && LOG2N <= 12, "grid size 16..4096");
 };
 
@@ -404,11 +413,11 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, CC = GG::CC, FB = GG::FB;
   // FP32 with the DS multiplier: the e^{-2 pi i n/M} factors of the odd chain
-  // and the row-dependent parts of m1 ((a dk_y)^2 and e^{-(a dk_y)^2/sigma^2},
-  // a = |qbar_y|, the same for every column) come from shared tables filled
-  // once per CTA with the arithmetic of twm() and mult_high(), so the results
-  // are unchanged
+  // come from a shared table filled once per CTA with the arithmetic of twm(),
+  // and m1 of the item's columns from the plan's FP64-computed table, copied
+  // row by row into shared memory (cp.async) one item ahead
   constexpr bool TAB = GG::COL_TAB && !GEN;
+  constexpr int LDM = GG::LDM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* sm = stw + GG::STWP;
@@ -419,21 +428,29 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
   cpx<R>* buf_e = sm + (2 * cl) * FB;
   cpx<R>* buf_o = buf_e + FB;
   cpx<R>* wtab = sm + 2 * CC * FB;                       // N entries (TAB only)
-  // N + 1 entries (TAB only), even a first then odd a: a warp reads a's of
-  // one parity (a = |qbar| of the rows 2 (t + G m) + h), so consecutive entries
-  float2* mtab = reinterpret_cast<float2*>(wtab + N);
+  // TAB: buffer b holds the m1 rows of an item's CC columns; a warp reads a's
+  // of one parity (a = |qbar| of the rows 2 (t + G m) + h), so consecutive
+  // entries of the parity-split rows
+  float* mrow = reinterpret_cast<float*>(wtab + N);
   constexpr int MH = N / 2 + 1;  // even entries
+  const int items = (ncols + CC - 1) / CC;
+  const int total = items * mem.count;
+  // every thread: its share of the m1 rows of item it2 into buffer b
+  auto fetch_mult = [&](int it2, int b) {
+    const int item2 = it2 % items;
+    for (int i = tid; i < CC * (LDM / 4); i += GG::T_C) {
+      const int c = i / (LDM / 4), k = i - c * (LDM / 4);
+      const int col2 = item2 * CC + c;
+      if (col2 < ncols) cp_async16(mrow + (b * CC + c) * LDM + 4 * k, mt.m1 + size_t(col2) * mt.ldm + 4 * k);
+    }
+    cp_async_commit();
+  };
   if constexpr (TAB) {
     for (int i = tid; i < N; i += GG::T_C) wtab[i] = twm(ay, i);
-    for (int i = tid; i <= N; i += GG::T_C) {
-      const R a2 = R(i * i);
-      mtab[(i & 1) ? MH + (i >> 1) : (i >> 1)] = make_float2(a2 * mt.dky2, exp2f(a2 * mt.neg_dky2_s2_log2e));
-    }
+    if (int(blockIdx.x) < total) fetch_mult(blockIdx.x, 0);  // (a plan table: no wait needed)
     __syncthreads();
   }
   grid_dep_wait();
-  const int items = (ncols + CC - 1) / CC;
-  const int total = items * mem.count;
   // the next item's column values are loaded into registers before the
   // current item's inverse transform (PF), hiding their latency
   constexpr bool PF = TAB && DSNU_COL_REGPF;
@@ -448,16 +465,21 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
   };
   if constexpr (PF)
     if (int(blockIdx.x) < total) load_col(blockIdx.x, xn);
+  int kk = 0;  // items done by this CTA (the multiplier buffer is kk & 1)
 #pragma unroll 1
-  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+  for (int it = blockIdx.x; it < total; it += gridDim.x, ++kk) {
     if (it + int(gridDim.x) >= total) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(member_at(mem, mi), off.A);
     const int col = item * CC + cl;
     const bool valid = col < ncols;
-    const R wx2 = valid ? mt.wx2[col] : R(0);
-    const R gx = valid ? mt.gx[col] : R(0);
+    const R wx2 = (!TAB && valid) ? mt.wx2[col] : R(0);
+    const R gx = (!TAB && valid) ? mt.gx[col] : R(0);
     const R kxc = (GEN && valid) ? mt.kx[col] : R(0);
+    // this thread's copies of the item's m1 rows have landed; the barriers of
+    // the forward transform below make every thread's copies visible
+    if constexpr (TAB) cp_async_wait_all();
+    const float* mr = mrow + ((kk & 1) * CC + cl) * LDM;
     cpx<R> e[16], o[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -477,15 +499,12 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
     for (int m = 0; m < 16; ++m) {
       const int q = 2 * (t + G * m);
       if constexpr (TAB) {
-        // m1 at rows q and q + 1 (a = |qbar|), branch-free; equal to mult_high
+        // m1 at rows q and q + 1 (a = |qbar|, of the parity of q + h)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int qq = q + h;
           const int a = (qq < N) ? qq : 2 * N - qq;
-          const float2 tv = mtab[(h ? MH : 0) + (a >> 1)];  // a has the parity of qq
-          const R s = wx2 + tv.x;
-          const R part = mt.sharp ? ((s > mt.cut2) ? R(1) : R(0)) : (R(1) - (R(1) - gx) * tv.y);
-          const R mv = (s == R(0) || !valid) ? R(0) : -fdiv(wx2, (s == R(0)) ? R(1) : s) * part;
+          const R mv = valid ? mr[(h ? MH : 0) + (a >> 1)] : R(0);
           if (h == 0) e[m] = e[m] * mv;
           else o[m] = o[m] * mv;
         }
@@ -496,6 +515,10 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
     }
     if constexpr (PF)
       if (it + int(gridDim.x) < total) load_col(it + gridDim.x, xn);
+    // the next item's m1 rows into the other buffer (last read by the item
+    // before this one, whose reads the barriers since then have completed)
+    if constexpr (TAB)
+      if (it + int(gridDim.x) < total) fetch_mult(it + gridDim.x, (kk + 1) & 1);
     block_fft2_regs<R, LOG2N>(e, o, buf_e, buf_o, t, stw, cj == 0);
     if (valid) {
 #pragma unroll

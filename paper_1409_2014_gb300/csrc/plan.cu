@@ -451,6 +451,52 @@ static dsnu_status setup_spread(dsnu_plan_s* P, const std::vector<int2>& q0, con
   return DSNU_OK;
 }
 
+// The column multiplier of I1 (eq. SubInt1) on the padded grid,
+//   m1(q_x, a) = -(q_x dk_x)^2 / s * (1 - p),  s = (q_x dk_x)^2 + (a dk_y)^2,
+// with p = e^{-s/sigma^2} (Gaussian partition) or the indicator of s <= P^2
+// (sharp), m1 = 0 at s = 0; computed in FP64 and rounded once to FP32.  Row
+// q_x holds a = 2 j at j <= ny/2 and a = 2 j' + 1 at ny/2 + 1 + j', then zeros
+// up to its ldm = ny + 4 floats.
+__global__ void k_fill_m1(float* tab, int nx1, int ny, int ldm, double dkx, double dky, double inv_sigma2,
+                          int sharp, double cut2) {
+  const long long n = (long long)nx1 * ldm;
+  const int mh = ny / 2 + 1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int col = int(i / ldm), j = int(i - (long long)col * ldm);
+    float v = 0.0f;
+    if (j <= ny) {
+      const int a = (j < mh) ? 2 * j : 2 * (j - mh) + 1;
+      const double wx = col * dkx, wy = a * dky;
+      const double wx2 = wx * wx, s = wx2 + wy * wy;
+      if (s > 0.0) {
+        const double part = sharp ? (s > cut2 ? 1.0 : 0.0) : -expm1(-s * inv_sigma2);
+        v = float(-wx2 / s * part);
+      }
+    }
+    tab[i] = v;
+  }
+}
+
+static dsnu_status build_m1_table(dsnu_plan_s* P, double dkx, double dky, cudaStream_t st) {
+  const PlanGeom& g = P->geom;
+  const int ldm = g.ny + 4;
+  const size_t bytes = size_t(g.nx + 1) * ldm * sizeof(float);
+  void* m = nullptr;
+  cudaError_t e = cudaMalloc(&m, bytes);
+  if (e != cudaSuccess) return fail(DSNU_ENOMEM, std::string("cudaMalloc(multiplier table): ") + cudaGetErrorString(e));
+  k_fill_m1<<<1024, 256, 0, st>>>(static_cast<float*>(m), g.nx + 1, g.ny, ldm, dkx, dky,
+                                  1.0 / (g.sigma * g.sigma), g.sharp, g.cut_radius * g.cut_radius);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(m);
+    return fail(DSNU_ECUDA, std::string("multiplier table: ") + cudaGetErrorString(e));
+  }
+  P->m1_block = m;
+  P->tab.m1tab = static_cast<float*>(m);
+  return DSNU_OK;
+}
+
 template <typename R>
 static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   const dsnu_params& p = P->prm;
@@ -580,6 +626,10 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   t.status = reinterpret_cast<int*>(d + o_st);
   P->table_block = dev;
   P->table_bytes = b.bytes.size();
+  if (sizeof(R) == 4 && !g.m_generic) {
+    const dsnu_status sm = build_m1_table(P, dkx, dky, st);
+    if (sm != DSNU_OK) return sm;
+  }
   return setup_spread<R>(P, T.node_q0, T.node_w, st);
 }
 
@@ -750,6 +800,7 @@ dsnu_status dsnu_plan_create_multiplier(const dsnu_params* params, const dsnu_mu
     s = (p.precision == DSNU_MIXED) ? build_tables<float>(P, st) : build_tables<double>(P, st);
   if (s != DSNU_OK) {
     if (P->spread_block) cudaFree(P->spread_block);
+    if (P->m1_block) cudaFree(P->m1_block);
     if (P->table_block) cudaFree(P->table_block);
     delete P;
     return s;
@@ -757,6 +808,7 @@ dsnu_status dsnu_plan_create_multiplier(const dsnu_params* params, const dsnu_mu
   const cudaError_t e = (p.precision == DSNU_MIXED) ? prepare_kernels_f32(g) : prepare_kernels_f64(g);
   if (e != cudaSuccess) {
     if (P->spread_block) cudaFree(P->spread_block);
+    if (P->m1_block) cudaFree(P->m1_block);
     cudaFree(P->table_block);
     delete P;
     return fail(DSNU_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
@@ -867,6 +919,7 @@ dsnu_status dsnu_plan_destroy(dsnu_plan plan) {
     }
   }
   if (plan->spread_block) cudaFree(plan->spread_block);
+  if (plan->m1_block) cudaFree(plan->m1_block);
   cudaError_t e = cudaFree(plan->table_block);
   delete plan;
   if (e != cudaSuccess) return fail(DSNU_ECUDA, std::string("cudaFree: ") + cudaGetErrorString(e));
