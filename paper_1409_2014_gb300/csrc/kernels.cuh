@@ -375,27 +375,37 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     }
     __syncthreads();
     // separate the spectra at every q in [0, N] (rows fastest):
-    // Z(q) = E[q/2] (q even) or O[(q-1)/2] (q odd); Z(M - q) has the same parity
-    for (int idx = tid; idx < RB * (N + 1); idx += T) {
-      const int r2 = idx & (RB - 1), q = idx / RB, row2 = row0 + r2;
-      if (row2 >= ny) continue;
+    // Z(q) = E[q/2] (q even) or O[(q-1)/2] (q odd); Z(M - q) has the same parity.
+    // Element idx = tid + T i of the RB (N + 1) is row r2 = tid % RB (T is a
+    // multiple of RB) at q = tid / RB + G i: 16 steps for every thread, a 17th
+    // (q = N) for tid < RB; the row, and for G even the parity, stay fixed
+    {
+      const int r2 = tid & (RB - 1), q0 = tid / RB, row2 = row0 + r2;
       const cpx<R>* be = sm + (2 * r2) * RS;
       const cpx<R>* bo = be + RS;
-      const int k = q >> 1;
-      cpx<R> zq, zm;
-      if (q & 1) {
-        zq = bo[pad16(k)];
-        zm = bo[pad16(N - 1 - k)];
-      } else {
-        zq = be[pad16(k)];
-        zm = be[pad16(k == 0 ? 0 : N - k)];
-      }
-      A[Tile<R>::at(row2, q, ldqA)] = mk<R>(R(0.5) * (zq.x + zm.x), R(0.5) * (zq.y - zm.y));
-      if (q <= Q) {
-        const cpx<R> d = mk<R>(zq.x - zm.x, zq.y + zm.y);  // Z(q) - conj Z(M - q)
-        // divided by 2 i (by 2 (-i) in the conjugated pipeline)
-        B[Tile<R>::at(row2, q, ldqB)] = cj ? mk<R>(R(-0.5) * d.y, R(0.5) * d.x)
-                                           : mk<R>(R(0.5) * d.y, R(-0.5) * d.x);
+      cpx<R>* Ar = A + Tile<R>::at(row2, 0, ldqA);
+      cpx<R>* Br = B + Tile<R>::at(row2, 0, ldqB);
+      if (row2 < ny) {
+#pragma unroll 4
+        for (int i = 0; i < 17; ++i) {
+          const int q = q0 + G * i;
+          if (i == 16 && q > N) break;
+          const int k = q >> 1;
+          cpx<R> zq, zm;
+          if (q & 1) {
+            zq = bo[pad16(k)];
+            zm = bo[pad16(N - 1 - k)];
+          } else {
+            zq = be[pad16(k)];
+            zm = be[pad16(k == 0 ? 0 : N - k)];
+          }
+          Ar[q * Tile<R>::TR] = mk<R>(R(0.5) * (zq.x + zm.x), R(0.5) * (zq.y - zm.y));
+          if (q <= Q) {
+            const cpx<R> d = mk<R>(zq.x - zm.x, zq.y + zm.y);  // Z(q) - conj Z(M - q)
+            // divided by 2 i (by 2 (-i) in the conjugated pipeline)
+            Br[q * Tile<R>::TR] = cj ? mk<R>(R(-0.5) * d.y, R(0.5) * d.x) : mk<R>(R(0.5) * d.y, R(-0.5) * d.x);
+          }
+        }
       }
     }
   }
