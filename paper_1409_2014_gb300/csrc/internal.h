@@ -39,8 +39,8 @@ struct PlanTables {
   int2* ent_q0;   // per entry: stencil origin of the node
   void* ent_w;    // real, per entry: the node's 2w ES weights
   int* status;    // one int
-  float* m1tab;   // FP32 split plans with the DS multiplier: m1(q_x, |qbar_y|), (nx + 1) rows of ny + 4
-                  // floats, each row's even |qbar_y| first (see MultTabs::m1); else NULL
+  void* m1tab;    // split plans with the DS multiplier: m1(q_x, |qbar_y|) in the plan's precision,
+                  // (nx + 1) rows of ny + 4 entries, each row's even |qbar_y| first (MultTabs::m1); else NULL
 };
 
 

@@ -118,11 +118,11 @@ struct MultTabs {
   R a0, ac, as2;      // as2 = 2 as
   R dky;              // dk_y
   const R* kx;        // k_x of column q_x for the sin 2theta term (0 at the Nyquist column)
-  // FP32 plans with the DS multiplier: m1(q_x, a) for a = |qbar_y| <= N_y,
-  // computed in FP64 at plan creation, one row of ldm floats per column with
-  // the even a first (a = 2 j at j) and the odd a after them (a = 2 j' + 1 at
-  // N_y/2 + 1 + j')
-  const float* m1;
+  // plans with the DS multiplier: m1(q_x, a) for a = |qbar_y| <= N_y,
+  // computed in FP64 at plan creation (stored in the plan's precision), one
+  // row of ldm entries per column with the even a first (a = 2 j at j) and the
+  // odd a after them (a = 2 j' + 1 at N_y/2 + 1 + j')
+  const R* m1;
   int ldm;
 };
 
@@ -515,6 +515,18 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
           const int qq = q + h;
           const int a = (qq < N) ? qq : 2 * N - qq;
           const R mv = valid ? mr[(h ? MH : 0) + (a >> 1)] : R(0);
+          if (h == 0) e[m] = e[m] * mv;
+          else o[m] = o[m] * mv;
+        }
+      } else if constexpr (!GEN) {
+        // FP64: m1 read from the plan's table in global memory (the pass is
+        // bound by FP64 arithmetic, which the table saves; the loads overlap it)
+        const R* mg = mt.m1 + size_t(valid ? col : 0) * mt.ldm;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int qq = q + h;
+          const int a = (qq < N) ? qq : 2 * N - qq;
+          const R mv = valid ? mg[(h ? MH : 0) + (a >> 1)] : R(0);
           if (h == 0) e[m] = e[m] * mv;
           else o[m] = o[m] * mv;
         }

@@ -216,8 +216,8 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
                        g.n_gy, R(1.0 / (g.sigma * g.sigma)),
                        R(-g.dky2 / (g.sigma * g.sigma) * 1.4426950408889634), R(g.dky2), g.ny, g.sharp,
                        R(g.cut_radius * g.cut_radius), g.m_generic, g.m_alpha, R(g.m_a0), R(g.m_ac),
-                       R(2.0 * g.m_as), R(std::sqrt(g.dky2)), static_cast<const R*>(t.m_kx), t.m1tab,
-                       g.ny + 4};
+                       R(2.0 * g.m_as), R(std::sqrt(g.dky2)), static_cast<const R*>(t.m_kx),
+                       static_cast<const R*>(t.m1tab), g.ny + 4};
   const R* dcy = static_cast<const R*>(t.decon_y);
   const R* wts = static_cast<const R*>(t.node_w);
   const int ldqA = L.ldqA, ldqB = L.ldqB;

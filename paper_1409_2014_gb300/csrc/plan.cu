@@ -454,38 +454,40 @@ static dsnu_status setup_spread(dsnu_plan_s* P, const std::vector<int2>& q0, con
 // The column multiplier of I1 (eq. SubInt1) on the padded grid,
 //   m1(q_x, a) = -(q_x dk_x)^2 / s * (1 - p),  s = (q_x dk_x)^2 + (a dk_y)^2,
 // with p = e^{-s/sigma^2} (Gaussian partition) or the indicator of s <= P^2
-// (sharp), m1 = 0 at s = 0; computed in FP64 and rounded once to FP32.  Row
-// q_x holds a = 2 j at j <= ny/2 and a = 2 j' + 1 at ny/2 + 1 + j', then zeros
-// up to its ldm = ny + 4 floats.
-__global__ void k_fill_m1(float* tab, int nx1, int ny, int ldm, double dkx, double dky, double inv_sigma2,
-                          int sharp, double cut2) {
+// (sharp), m1 = 0 at s = 0; computed in FP64 and stored in the plan's
+// precision (one rounding for FP32).  Row q_x holds a = 2 j at j <= ny/2 and
+// a = 2 j' + 1 at ny/2 + 1 + j', then zeros up to its ldm = ny + 4 entries.
+template <typename T>
+__global__ void k_fill_m1(T* tab, int nx1, int ny, int ldm, double dkx, double dky, double inv_sigma2, int sharp,
+                          double cut2) {
   const long long n = (long long)nx1 * ldm;
   const int mh = ny / 2 + 1;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int col = int(i / ldm), j = int(i - (long long)col * ldm);
-    float v = 0.0f;
+    T v = T(0);
     if (j <= ny) {
       const int a = (j < mh) ? 2 * j : 2 * (j - mh) + 1;
       const double wx = col * dkx, wy = a * dky;
       const double wx2 = wx * wx, s = wx2 + wy * wy;
       if (s > 0.0) {
         const double part = sharp ? (s > cut2 ? 1.0 : 0.0) : -expm1(-s * inv_sigma2);
-        v = float(-wx2 / s * part);
+        v = T(-wx2 / s * part);
       }
     }
     tab[i] = v;
   }
 }
 
+template <typename R>
 static dsnu_status build_m1_table(dsnu_plan_s* P, double dkx, double dky, cudaStream_t st) {
   const PlanGeom& g = P->geom;
   const int ldm = g.ny + 4;
-  const size_t bytes = size_t(g.nx + 1) * ldm * sizeof(float);
+  const size_t bytes = size_t(g.nx + 1) * ldm * sizeof(R);
   void* m = nullptr;
   cudaError_t e = cudaMalloc(&m, bytes);
   if (e != cudaSuccess) return fail(DSNU_ENOMEM, std::string("cudaMalloc(multiplier table): ") + cudaGetErrorString(e));
-  k_fill_m1<<<1024, 256, 0, st>>>(static_cast<float*>(m), g.nx + 1, g.ny, ldm, dkx, dky,
-                                  1.0 / (g.sigma * g.sigma), g.sharp, g.cut_radius * g.cut_radius);
+  k_fill_m1<R><<<1024, 256, 0, st>>>(static_cast<R*>(m), g.nx + 1, g.ny, ldm, dkx, dky, 1.0 / (g.sigma * g.sigma),
+                                     g.sharp, g.cut_radius * g.cut_radius);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -493,7 +495,7 @@ static dsnu_status build_m1_table(dsnu_plan_s* P, double dkx, double dky, cudaSt
     return fail(DSNU_ECUDA, std::string("multiplier table: ") + cudaGetErrorString(e));
   }
   P->m1_block = m;
-  P->tab.m1tab = static_cast<float*>(m);
+  P->tab.m1tab = m;
   return DSNU_OK;
 }
 
@@ -626,8 +628,8 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   t.status = reinterpret_cast<int*>(d + o_st);
   P->table_block = dev;
   P->table_bytes = b.bytes.size();
-  if (sizeof(R) == 4 && !g.m_generic) {
-    const dsnu_status sm = build_m1_table(P, dkx, dky, st);
+  if (!g.m_generic) {
+    const dsnu_status sm = build_m1_table<R>(P, dkx, dky, st);
     if (sm != DSNU_OK) return sm;
   }
   return setup_spread<R>(P, T.node_q0, T.node_w, st);
