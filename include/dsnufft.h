@@ -118,9 +118,10 @@ typedef struct {
  * The spreading tile configuration is chosen by timing the candidates on the
  * device (temporary scratch, cached per device and parameters for the
  * process); DSNU_AUTOTUNE=0 in the environment keeps the default one.
- * Mixed plans with the DS multiplier also tabulate the column multiplier
- * m1(q_x, |qbar_y|) of I1 on the device in FP64, rounded once to FP32
- * ((nx + 1) (ny + 4) floats: 67 MB at 4096 x 4096).
+ * Plans with the DS multiplier also tabulate the column multiplier
+ * m1(q_x, |qbar_y|) of I1 on the device in FP64, stored in the plan's
+ * precision ((nx + 1) (ny + 4) entries: 67 MB mixed, 134 MB FP64 at
+ * 4096 x 4096).
  * Ownership: the plan owns its tables (device memory, freed by
  * dsnu_plan_destroy); it does not own the workspace.
  * Errors: DSNU_EINVAL (bad params, *out untouched), DSNU_ENOMEM, DSNU_ECUDA. */
