@@ -21,9 +21,11 @@
  *   - Arrays are row-major [ny][nx] (x fastest), i.e. a (ny, nx) tensor.
  *   - Pointers named *_dev are DEVICE pointers; the caller owns them.
  *   - Calls that take a stream enqueue work on it and return at once
- *     (stream == NULL means the legacy default stream).  No call synchronises
- *     the device except dsnu_plan_create (final table upload) and
- *     dsnu_status_poll.
+ *     (stream == NULL means the legacy default stream).  Only the calls that
+ *     build or free state wait for the GPU (dsnu_plan_create and
+ *     dsnu_ds_plan_create for their table uploads, dsnu_batch_bind for its
+ *     member tables, the destroy calls for the plan's own streams), besides
+ *     dsnu_profile_end and dsnu_status_poll, which read results back.
  *   - Errors: every call returns a dsnu_status.  Invalid arguments give
  *     DSNU_EINVAL before any launch.  dsnu_last_error() returns a
  *     thread-local message for the last failing call on this thread.
