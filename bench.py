@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -149,11 +150,25 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- helpers
 
-def kernel_hash() -> str:
+def code_only(src: str) -> str:
+    """CUDA/C++ source without its comments and with whitespace runs collapsed:
+    what the kernel hash covers, so that editing a comment does not mark the
+    recorded counters stale (no string literal in the hashed files holds //)."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return " ".join(src.split())
+
+
+def kernel_hash(read=None) -> str:
+    """Hash of the code of the pipeline's kernel sources; `read(name)` returns
+    a file's text (default: the working tree)."""
+    if read is None:
+        def read(name):
+            with open(os.path.join(ROOT, "paper_1409_2014_gb300", "csrc", name), encoding="utf-8") as fh:
+                return fh.read()
     h = hashlib.sha256()
     for f in ("common.cuh", "kernels.cuh", "pipeline.cuh"):
-        with open(os.path.join(ROOT, "paper_1409_2014_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        h.update(code_only(read(f)).encode())
     return h.hexdigest()[:16]
 
 

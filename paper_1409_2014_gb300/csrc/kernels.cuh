@@ -57,22 +57,24 @@
 #ifndef DSNU_COL_PAIRED
 #define DSNU_COL_PAIRED 1
 #endif
-// Inverse row pass: Phi rows written by bulk copies from shared memory
-// (measured slower than direct 16-byte stores at 4096^2, so off)
-// Forward row pass: bulk prefetch of the next rows of rho (FP32 plans)
+// Forward row pass: bulk prefetch of the next rows of rho (FP32 plans), with
+// the landing rows N + DSNU_ROWF_LPAD doubles apart
 #ifndef DSNU_ROWF_PF
 #define DSNU_ROWF_PF 1
 #endif
 #ifndef DSNU_ROWF_LPAD
 #define DSNU_ROWF_LPAD 8
 #endif
+// Inverse row pass: the band values prefetched with the row pair when they
+// fit (BPF); asynchronous prefetch of the next row pair of A (FP32, PF)
 #ifndef DSNU_ROWI_BPF
 #define DSNU_ROWI_BPF 1
 #endif
-// Inverse row pass: asynchronous prefetch of the next row pair of A (FP32)
 #ifndef DSNU_ROWI_PF
 #define DSNU_ROWI_PF 1
 #endif
+// Column pass: the next column loaded into registers during the current
+// inverse transform
 #ifndef DSNU_COL_REGPF
 #define DSNU_COL_REGPF 1
 #endif
