@@ -123,3 +123,23 @@ def _mut_no_padding(monkeypatch):
 def test_mutation_is_caught(monkeypatch, mutation):
     mutation(monkeypatch)
     assert not _battery()
+
+
+def test_reversed_sharp_indicator_is_caught(monkeypatch):
+    """The sharp partition's pin (a decayed tail: I1 vanishes, I2 carries the
+    closed form) catches an indicator taken outside the disk instead of
+    inside; the total alone would not, the split being exact for any p."""
+    orig = OP.partition
+
+    def part(w2, p):
+        if p.partition == "sharp":
+            return (w2 > p.cut_radius ** 2).astype(float)
+        return orig(w2, p)
+    monkeypatch.setattr(OP, "partition", part)
+    n, L = 128, 16.0
+    x = O.grid_axis(n, L)
+    X, Y = np.meshgrid(x, x)
+    p = OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=10.0, n_r=120, n_theta=244, partition="sharp")
+    phi, i1, i2 = O.solve(np.exp(-(X**2 + Y**2)), p, return_parts=True)
+    scale = np.abs(O.gaussian_potential(X, Y)).max()
+    assert np.abs(i1).max() / scale > 5e-11

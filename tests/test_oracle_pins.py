@@ -256,3 +256,19 @@ def test_rectangular_grid_closed_form():
     X, Y = np.meshgrid(x, y)
     phi = O.solve(np.exp(-(X**2 + Y**2)), p)
     assert rel_linf(phi, O.gaussian_potential(X, Y)) < 1e-13
+
+
+def test_sharp_partition_with_a_decayed_tail_reduces_to_the_polar_quadrature():
+    """Sharp split (p = 1 on |k| <= P) for rho = exp(-r^2), whose transform
+    pi exp(-|k|^2/4) integrates to e^{-P^2/4} (= 1.4e-11 at P = 10) outside the
+    disk: I1 then vanishes to that level, and I2 alone, with the polar rule
+    resolved (n_theta > P R, R the half-diagonal), carries the closed form."""
+    n, L = 128, 16.0
+    X, Y = _grid(n, L)
+    p = OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=10.0, n_r=120, n_theta=244, partition="sharp")
+    phi, i1, i2 = O.solve(np.exp(-(X**2 + Y**2)), p, return_parts=True)
+    ex = O.gaussian_potential(X, Y)
+    scale = np.abs(ex).max()
+    assert np.abs(i1).max() / scale < 5e-11
+    assert np.abs(i2 - ex).max() / scale < 5e-11
+    assert rel_linf(phi, ex) < 1e-12
