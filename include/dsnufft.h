@@ -54,9 +54,17 @@ typedef enum {
   DSNU_FP64 = 0,   /* every step in FP64 */
   DSNU_MIXED = 1   /* FFT butterflies, ES spreading/interpolation in FP32;
                       nodes, weights, twiddle/phase tables generated in FP64;
-                      the per-node low-frequency weighting in FP64;
+                      the per-node low-frequency weighting in FP64; the final
+                      accumulation Phi = I1 + I2 in FP64 (dsnu_accumulation);
                       rho in and Phi out are FP64 */
 } dsnu_precision;
+
+/* How a mixed plan forms Phi = I1 + I2 (eq. PotSplitWhoSpace) from the two
+ * FP32 terms of its last pass.  FP64 plans always work in FP64. */
+typedef enum {
+  DSNU_ACCUM_FP64 = 0,    /* each term widened to FP64 (exactly) and added in FP64 */
+  DSNU_ACCUM_WORKING = 1  /* added in FP32, the sum widened at the store */
+} dsnu_accumulation;
 
 typedef enum {
   DSNU_PARTITION_GAUSS = 0,  /* p(k) = exp(-|k|^2/sigma^2) (Sec. 2.1) */
@@ -93,7 +101,7 @@ typedef struct {
   int32_t precision;       /* dsnu_precision */
   int32_t partition;       /* dsnu_partition */
   int32_t radial_rule;     /* dsnu_radial_rule of the polar quadrature */
-  int32_t reserved;        /* set to 0 */
+  int32_t accumulation;    /* dsnu_accumulation of mixed plans; 0 = FP64 */
 } dsnu_params;
 
 typedef struct dsnu_plan_s* dsnu_plan;

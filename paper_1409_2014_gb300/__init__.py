@@ -21,20 +21,23 @@ from ._abi import (  # noqa: F401
 _PREC = {"fp64": DSNU_FP64, "mixed": DSNU_MIXED}
 _PART = {"gauss": DSNU_PARTITION_GAUSS, "sharp": DSNU_PARTITION_SHARP, "none": DSNU_PARTITION_NONE}
 _RADIAL = {"legendre": _abi.DSNU_RADIAL_LEGENDRE, "jacobi": _abi.DSNU_RADIAL_JACOBI}
+_ACCUM = {"fp64": _abi.DSNU_ACCUM_FP64, "working": _abi.DSNU_ACCUM_WORKING}
 
 
 def make_params(nx, ny, lx, ly, cut_radius, n_r, n_theta, sigma=0.0, kernel_width=0,
-                precision="fp64", partition="gauss", radial="legendre") -> dsnu_params:
+                precision="fp64", partition="gauss", radial="legendre", accumulation="fp64") -> dsnu_params:
     """partition "none" selects the standard periodic FFT solver (no split, no
     padding: pad_factor 1); the polar parameters are then ignored.  radial:
-    "legendre" or "jacobi" (the radial rule of the polar quadrature)."""
+    "legendre" or "jacobi" (the radial rule of the polar quadrature).
+    accumulation: how a mixed plan adds Phi = I1 + I2, "fp64" (each FP32 term
+    widened and added in FP64) or "working" (added in FP32)."""
     standard = partition == "none"
     return dsnu_params(nx=int(nx), ny=int(ny), lx=float(lx), ly=float(ly),
                        cut_radius=float(cut_radius or 0.0), sigma=float(sigma), n_r=int(n_r or 0),
                        n_theta=int(n_theta or 0), kernel_width=int(kernel_width),
                        pad_factor=1 if standard else 2,
                        precision=_PREC[precision], partition=_PART[partition],
-                       radial_rule=_RADIAL[radial], reserved=0)
+                       radial_rule=_RADIAL[radial], accumulation=_ACCUM[accumulation])
 
 
 class Plan:
@@ -47,7 +50,7 @@ class Plan:
 
     def __init__(self, nx, ny=None, lx=None, ly=None, cut_radius=None, n_r=None, n_theta=None,
                  sigma=0.0, kernel_width=0, precision="fp64", partition="gauss", radial="legendre",
-                 device=None, params=None, multiplier=None):
+                 device=None, params=None, multiplier=None, accumulation="fp64"):
         import torch
 
         ny = nx if ny is None else ny
@@ -59,7 +62,8 @@ class Plan:
             dev = torch.device("cuda", torch.cuda.current_device())
         self.device = dev
         self.params = params if params is not None else make_params(
-            nx, ny, lx, ly, cut_radius, n_r, n_theta, sigma, kernel_width, precision, partition, radial)
+            nx, ny, lx, ly, cut_radius, n_r, n_theta, sigma, kernel_width, precision, partition, radial,
+            accumulation)
         self.shape = (int(ny), int(nx))
         self._handle = None
         with torch.cuda.device(self.device):

@@ -17,6 +17,7 @@ DSNU_OK, DSNU_EINVAL, DSNU_ENOMEM, DSNU_ECUDA, DSNU_ETIMEOUT, DSNU_EUNSUPPORTED 
 DSNU_FP64, DSNU_MIXED = 0, 1
 DSNU_PARTITION_GAUSS, DSNU_PARTITION_SHARP, DSNU_PARTITION_NONE = 0, 1, 2
 DSNU_RADIAL_LEGENDRE, DSNU_RADIAL_JACOBI = 0, 1
+DSNU_ACCUM_FP64, DSNU_ACCUM_WORKING = 0, 1
 
 STATUS_NAMES = {0: "DSNU_OK", 1: "DSNU_EINVAL", 2: "DSNU_ENOMEM", 3: "DSNU_ECUDA",
                 4: "DSNU_ETIMEOUT", 5: "DSNU_EUNSUPPORTED"}
@@ -31,6 +32,7 @@ EXPORTED = [
     "dsnu_batch_create", "dsnu_batch_workspace_bytes", "dsnu_batch_bind", "dsnu_batch_capture_graph",
     "dsnu_batch_solve", "dsnu_batch_destroy", "dsnu_radial_nodes", "dsnu_params_auto",
     "dsnu_plan_create_multiplier", "dsnu_stream_staging_bytes", "dsnu_solve_host_stream",
+    "dsnu_measure_fma_peak",
 ]
 
 
@@ -42,7 +44,7 @@ class dsnu_params(ctypes.Structure):
         ("n_r", ctypes.c_int32), ("n_theta", ctypes.c_int32),
         ("kernel_width", ctypes.c_int32), ("pad_factor", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("partition", ctypes.c_int32),
-        ("radial_rule", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("radial_rule", ctypes.c_int32), ("accumulation", ctypes.c_int32),
     ]
 
 
@@ -138,6 +140,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dsnu_solve_noalloc.restype = st
     lib.dsnu_noalloc_scratch_bytes.argtypes = []
     lib.dsnu_noalloc_scratch_bytes.restype = ctypes.c_size_t
+    lib.dsnu_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), vp]
+    lib.dsnu_measure_fma_peak.restype = st
     d = ctypes.c_double
     lib.dsnu_ds_plan_create.argtypes = [ctypes.POINTER(dsnu_ds_params), vp, ctypes.POINTER(vp)]
     lib.dsnu_ds_set_linear_step.argtypes = [vp, d, d, vp]
@@ -295,6 +299,15 @@ def dsnu_solve_noalloc(plan: int, rho_ptr: int, phi_ptr: int, stream: int = 0) -
 
 def dsnu_noalloc_scratch_bytes() -> int:
     return int(load().dsnu_noalloc_scratch_bytes())
+
+
+def dsnu_measure_fma_peak(precision: int, stream: int = 0) -> float:
+    """Measured FMA throughput of the current device in flop/s (DSNU_FP64 or
+    DSNU_MIXED for FP32)."""
+    out = ctypes.c_double()
+    _check(load().dsnu_measure_fma_peak(ctypes.c_int32(precision), ctypes.byref(out), ctypes.c_void_p(stream)),
+           "dsnu_measure_fma_peak")
+    return float(out.value)
 
 
 def _vp(x):

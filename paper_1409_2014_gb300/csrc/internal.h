@@ -79,6 +79,7 @@ struct PlanGeom {
   int spread_cfg;          // index into kSpreadCfgs (chosen by the autotuner)
   int spread_tile;         // its tile edge (cells)
   int precision, sharp;
+  int acc64;     // mixed plans: Phi = I1 + I2 added in FP64 (dsnu_accumulation)
   int standard;  // 1: the standard periodic FFT solver (kappa = 1, p = 0; standard.cuh)
   int pdl;       // 1: pipeline kernels launched with programmatic dependent launch
   // multiplier |k|^alpha (a0 + ac cos 2theta + as sin 2theta) when m_generic (else -k_x^2/|k|^2)

@@ -22,7 +22,8 @@
 //   k_band_inv: per band column: inverse column DFT of S, N rows.
 //   k_row_inv : per row: one inverse length-M DFT of W = Y + i S
 //               (Hermitian extension of both), keeping N points;
-//               Phi = [Re T + Im T dx dy] / (Mx My)   (I1 + I2, eq. PotSplitWhoSpace).
+//               Phi = [Re T + Im T dx dy] / (Mx My)   (I1 + I2, eq. PotSplitWhoSpace;
+//               in mixed plans each term widened to FP64 and the sum formed in FP64).
 //
 // Intermediate spectra (A, B and the inverse band columns) are stored
 // row-tiled: element (row iy, column q) at [iy / TR][q][iy % TR] with TR rows
@@ -337,10 +338,11 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     const int row = row0 + rr;
     const bool valid = row < ny;
     const R dy = valid ? decon_y[row] : R(0);
+    bool landed = true;
     if constexpr (PF) {
-      // bounded wait (1 s): on expiry the status word records it and the
-      // item runs on whatever the buffer holds
-      if (!mbar_wait(bar, phase, 1000000000ull)) atomicExch(status, int(DSNU_ETIMEOUT));
+      // bounded wait (1 s); on expiry the CTA stops after the reads below
+      // (cta_timed_out) without writing anything
+      landed = mbar_wait(bar, phase, 1000000000ull);
       phase ^= 1u;
     }
     cpx<R> e[16], o[16];
@@ -365,7 +367,8 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
       o[m] = cmul(z, w);
     }
     if constexpr (PF) {
-      __syncthreads();  // every thread has read the landing buffer
+      // every thread has read the landing buffer (a barrier); stop if a wait expired
+      if (cta_timed_out(landed, bar, phase ^ 1u, status)) return;
       if (tid == 0 && it + int(gridDim.x) < total) prefetch(it + gridDim.x);
     }
     block_fft2_regs<R, LOG2N, PF>(e, o, buf_e, buf_o, t, stw, cj != 0);
@@ -916,11 +919,14 @@ k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs
 //   T(2j+1) = IDFT_N[(W(q) - W(q + N)) e^{+2 pi i q/M}](j),   q < N,
 // with W(q) = Y(q) + i S(q) for q <= N and W(M - q) = conj Y(q) + i conj S(q).
 // Both transforms run together; j < N/2 gives the grid points n < N.
-// Phi must be 16-byte aligned (checked on the host).
+// Phi must be 16-byte aligned (checked on the host).  With acc64 (FP32 plans)
+// Phi = I1 + I2 is added in FP64: I1 = Re T / (Mx My) and I2 = Im T dx dy /
+// (Mx My) are each formed in FP32 (1/(Mx My) is a power of two, so the
+// scaling is exact), widened exactly, and summed in FP64.
 template <typename R, int LOG2N>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(Geo<R, LOG2N>::MINB_I))
 k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
-          const R* __restrict__ decon_y, R scale, int cj, int bpf) {
+          const R* __restrict__ decon_y, R scale, int cj, int bpf, int acc64) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, RB = GG::RB_I, RS = GG::RS, T = GG::T_RI;
   constexpr bool PF = GG::ROWI_PF;
@@ -1058,15 +1064,29 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     double* __restrict__ phi = mb.phi;
     if (valid) {
       // slot m holds T(2 (t + G m)) in a and T(2 (t + G m) + 1) in b; n < N for m < 8
+      if (sizeof(R) == 4 && acc64) {
+        const R dys = dy * scale;
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        const int n = 2 * (t + G * m);
-        const R ia = cj ? -a[m].y : a[m].y;
-        const R ib = cj ? -b[m].y : b[m].y;
-        double2 out;
-        out.x = to_f64<R>((a[m].x + ia * ax.decon[n] * dy) * scale);
-        out.y = to_f64<R>((b[m].x + ib * ax.decon[n + 1] * dy) * scale);
-        *reinterpret_cast<double2*>(phi + size_t(row) * N + n) = out;
+        for (int m = 0; m < 8; ++m) {
+          const int n = 2 * (t + G * m);
+          const R ia = cj ? -a[m].y : a[m].y;
+          const R ib = cj ? -b[m].y : b[m].y;
+          double2 out;
+          out.x = to_f64<R>(a[m].x * scale) + to_f64<R>(ia * ax.decon[n] * dys);
+          out.y = to_f64<R>(b[m].x * scale) + to_f64<R>(ib * ax.decon[n + 1] * dys);
+          *reinterpret_cast<double2*>(phi + size_t(row) * N + n) = out;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int n = 2 * (t + G * m);
+          const R ia = cj ? -a[m].y : a[m].y;
+          const R ib = cj ? -b[m].y : b[m].y;
+          double2 out;
+          out.x = to_f64<R>((a[m].x + ia * ax.decon[n] * dy) * scale);
+          out.y = to_f64<R>((b[m].x + ib * ax.decon[n + 1] * dy) * scale);
+          *reinterpret_cast<double2*>(phi + size_t(row) * N + n) = out;
+        }
       }
     }
   }

@@ -249,7 +249,7 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
   launch_k(g.pdl != 0, k_row_inv<R, L2>,                                                            \
            dim3(persistent_grid(nm * ((g.ny + Geo<R, L2>::RB_I - 1) / Geo<R, L2>::RB_I), g.cap_rowi)), \
            dim3(Geo<R, L2>::T_RI), g.smem_rowi, st, mem, off, ldqA, ldqB, g.Q, g.ny, ax, dcy, R(g.scale), cj, \
-           g.rowi_bpf)
+           g.rowi_bpf, g.acc64)
 #define DSNU_MARK(I) \
   if (ev) cudaEventRecord(ev[I], st)
   // the band chain (type-2 columns, interpolation, weighting, spreading,

@@ -736,6 +736,8 @@ dsnu_status dsnu_plan_create_multiplier(const dsnu_params* params, const dsnu_mu
   if (!(p.lx > 0.0) || !(p.ly > 0.0) || !std::isfinite(p.lx) || !std::isfinite(p.ly))
     return fail(DSNU_EINVAL, "lx, ly must be positive and finite");
   if (p.precision != DSNU_FP64 && p.precision != DSNU_MIXED) return fail(DSNU_EINVAL, "unknown precision");
+  if (p.accumulation != DSNU_ACCUM_FP64 && p.accumulation != DSNU_ACCUM_WORKING)
+    return fail(DSNU_EINVAL, "unknown accumulation");
   if (p.partition != DSNU_PARTITION_GAUSS && p.partition != DSNU_PARTITION_SHARP &&
       p.partition != DSNU_PARTITION_NONE)
     return fail(DSNU_EINVAL, "unknown partition");
@@ -792,6 +794,7 @@ dsnu_status dsnu_plan_create_multiplier(const dsnu_params* params, const dsnu_mu
   g.cut_radius = p.cut_radius;
   g.n_nodes = p.n_r * p.n_theta;
   g.precision = p.precision;
+  g.acc64 = (p.precision == DSNU_MIXED && p.accumulation == DSNU_ACCUM_FP64) ? 1 : 0;
   g.sharp = (p.partition == DSNU_PARTITION_SHARP);
   g.scale = 1.0 / (double(g.mx) * double(g.my));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
