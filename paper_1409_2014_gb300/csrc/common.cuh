@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dsnufft.h"
+
 namespace dsnu {
 
 template <typename R>
@@ -459,6 +461,22 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
     if (global_ns() - t0 > ns) return false;
+  return true;
+}
+
+// The way out of a prefetching loop after a bounded wait expired in some
+// thread of the CTA (every thread calls it, with that thread's verdict): the
+// status word records the timeout, thread 0 waits (bounded again) for the copy
+// still in flight on phase `parity` of `bar`, so that the CTA does not exit
+// while data lands in its shared memory, and the caller returns without
+// writing results.  Returns true when the CTA must stop; it is a barrier for
+// the whole CTA either way.
+__device__ __forceinline__ bool cta_timed_out(bool ok, unsigned long long* bar, unsigned parity, int* status) {
+  if (!__syncthreads_or(!ok)) return false;
+  if (threadIdx.x == 0) {
+    atomicExch(status, int(DSNU_ETIMEOUT));
+    mbar_wait(bar, parity, 1000000000ull);
+  }
   return true;
 }
 

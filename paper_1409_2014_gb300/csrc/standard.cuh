@@ -93,8 +93,10 @@ k_std_row_fwd(Members mem, size_t offH, int ldq, int ny, const cpx<R>* __restric
     const int pr = item * PER + rr;
     const bool valid = pr < pairs;
     const int row = 2 * pr;
+    bool landed = true;
     if constexpr (PF) {
-      if (!mbar_wait(bar, phase, 1000000000ull)) atomicExch(status, int(DSNU_ETIMEOUT));
+      // bounded wait (1 s); on expiry the CTA stops after the reads below
+      landed = mbar_wait(bar, phase, 1000000000ull);
       phase ^= 1u;
     }
     cpx<R> v[16];
@@ -114,7 +116,8 @@ k_std_row_fwd(Members mem, size_t offH, int ldq, int ny, const cpx<R>* __restric
       v[m] = mk<R>(a, b);
     }
     if constexpr (PF) {
-      __syncthreads();  // every thread has read the landing buffer
+      // every thread has read the landing buffer (a barrier); stop if a wait expired
+      if (cta_timed_out(landed, bar, phase ^ 1u, status)) return;
       if (tid == 0 && it + int(gridDim.x) < total) prefetch(it + gridDim.x);
     }
     block_fft_regs<R, LOG2N, PF>(v, buf, t, stw, cj != 0);
