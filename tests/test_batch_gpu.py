@@ -1,9 +1,11 @@
 """Batched solves (ragged grid sizes, shared plans, CUDA graph replay) through
-the C ABI: every member equals its own dsnu_solve bit for bit."""
+the C ABI: every member equals its own dsnu_solve bit for bit, and one member
+of each grid size matches the FP64 oracle on a sample of its grid."""
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -67,6 +69,18 @@ def test_config5_batch_of_64():
     torch.cuda.synchronize()
     for (n, _, _), r, f in zip(members, rhos, phis):
         assert torch.equal(f, plans[n].solve(r))
+    # the first member of each size against the oracle (stride-n/128 sample)
+    seen = set()
+    for (n, k, s), f in zip(members, phis):
+        if n in seen:
+            continue
+        seen.add(n)
+        rows, cols = np.arange(1, n, n // 128), np.arange(2, n, n // 128)
+        op = oracle.OracleParams(nx=n, ny=n, lx=32.0, ly=32.0, cut_radius=8.0, n_r=64, n_theta=256)
+        ref = oracle.solve(synth.density_sum(n, n, 32.0, 32.0, seed=s, count=k), op, rows=rows, cols=cols)
+        got = f.cpu().numpy()[np.ix_(rows, cols)]
+        assert float(np.abs(got - ref).max() / np.abs(ref).max()) <= 1e-6, n
+    assert len(seen) == 4
     b.close()
     for p in plans.values():
         p.close()
