@@ -56,20 +56,22 @@ def parse():
 # --------------------------------------------------------------------------- oracle
 
 def oracle_sample(rho: np.ndarray, node_frac: float = 1.0):
-    """Time the FP64 oracle (as it stands) on a bounded sample of one solve of
-    the workload: I1 on the whole grid; the type-2 sums for a fraction of the
-    polar nodes; the type-1 sums for those nodes on the 512^2 stride-8
-    subsample.  Returns (estimated seconds for one full solve, phi on the
-    subsample when node_frac == 1 else None, description)."""
+    """The FP64 oracle (as it stands) on one solve of the workload, or on a
+    bounded sample of one: I1 on the whole grid, then both nonuniform direct
+    sums over every grid point for every round(1/node_frac)-th polar node.
+    The direct sums are linear in the number of nodes, so the time of a whole
+    solve is estimated as t(I1) + t(sums) / node_frac; with node_frac = 1 the
+    solve is complete and the time measured.  Returns (seconds for one whole
+    solve, {"phi", "i1"} full-grid arrays when node_frac == 1 else None,
+    description, component times)."""
     import oracle
 
     n, L = WL["n"], WL["L"]
     op = oracle.OracleParams(nx=n, ny=n, lx=L, ly=L, cut_radius=WL["P"], n_r=WL["n_r"],
                              n_theta=WL["n_theta"])
     x = oracle.grid_axis(n, L)
-    rows = np.arange(0, n, SUB)
     t0 = time.perf_counter()
-    i1 = oracle.i1_padded_fft(rho, op)[np.ix_(rows, rows)]
+    i1 = oracle.i1_padded_fft(rho, op)
     t1 = time.perf_counter()
     kx, ky, *_ = oracle.polar_nodes(op)
     D = oracle.polar_weights(op)
@@ -78,16 +80,19 @@ def oracle_sample(rho: np.ndarray, node_frac: float = 1.0):
     frac = take.size / m
     rh = oracle.rho_hat_direct(rho, x, x, kx[take], ky[take])
     t2 = time.perf_counter()
-    i2 = oracle.i2_direct_from_coeffs(D[take] * rh, kx[take], ky[take], x[rows], x[rows])
+    i2 = oracle.i2_direct_from_coeffs(D[take] * rh, kx[take], ky[take], x, x)
     t3 = time.perf_counter()
-    sub_pts = rows.size * rows.size
-    scale1 = (n * n) / sub_pts
-    est = (t1 - t0) + (t2 - t1) / frac + (t3 - t2) * scale1 / frac
-    desc = (f"one {n}^2 solve: I1 FFTs on the full grid; type-2 sums for {take.size} of {m} "
-            f"nodes (x{1 / frac:.0f}); type-1 sums for those nodes on the {rows.size}^2 stride-{SUB} "
-            f"subsample (x{scale1 / frac:.0f} to the full grid)")
-    phi = (i1 + i2) if take.size == m else None
-    return est, phi, desc, {"i1": t1 - t0, "type2": t2 - t1, "type1": t3 - t2}
+    est = (t1 - t0) + (t3 - t1) / frac
+    if take.size == m:
+        desc = (f"one complete {n}^2 solve (I1 by the padded FFT, both direct sums over all {m} polar "
+                f"nodes and all {n}^2 grid points), measured")
+        out = {"phi": i1 + i2, "i1": i1}
+    else:
+        desc = (f"one {n}^2 solve estimated from a sample: I1 on the full grid (measured) plus both direct "
+                f"sums over all {n}^2 grid points for {take.size} of {m} polar nodes (measured, scaled "
+                f"x{1 / frac:.0f}: the sums are linear in the node count)")
+        out = None
+    return est, out, desc, {"i1": t1 - t0, "type2": t2 - t1, "type1": t3 - t2, "node_frac": frac}
 
 
 # --------------------------------------------------------------------------- clocks
@@ -175,14 +180,16 @@ def kernel_hash(read=None) -> str:
 def algorithmic_bytes(stage: str, n: int, Q: int, csz: int, n_nodes: int, w: int, rsz: int,
                       n_items: int = 0, tile: int = 8) -> float:
     """Bytes one launch of a stage must move at minimum (inputs read once,
-    outputs written once), for an n x n grid with band half-width Q."""
+    outputs written once), for an n x n grid with band half-width Q.  Plan
+    tables that an implementation chooses to read (the column pass's
+    multiplier table) are not the method's work: see plan_table_bytes."""
     A = csz * n * (n + 1)           # half-spectrum intermediate
     Bc = csz * n * (Q + 1)          # band columns of the row spectra
     band = csz * (Q + 1) * (2 * Q + 1)
     nodes = n_nodes * (8 + 2 * w * rsz + 8 + csz)  # q0, weights, D, c
     return float({
         "row_fwd": 8 * n * n + A + Bc,
-        "col_main": 2 * A + (n + 1) * (n + 4) * 4 * (csz == 8),  # FP32: + the multiplier table rows
+        "col_main": 2 * A,
         "band_fwd": Bc + band,
         "interp": band + nodes,
         "spread": nodes + n_items * tile * tile * csz,     # node data in, one partial tile per item out
@@ -190,6 +197,39 @@ def algorithmic_bytes(stage: str, n: int, Q: int, csz: int, n_nodes: int, w: int
         "band_inv": band + Bc,
         "row_inv": A + Bc + 8 * n * n,
     }[stage])
+
+
+def plan_table_bytes(stage: str, n: int, rsz: int) -> float:
+    """Bytes of plan tables a launch reads beyond its algorithmic bytes: the
+    column pass's multiplier table m1 (n + 1 rows of n + 4 entries, in the
+    plan's precision), a trade of memory traffic for arithmetic."""
+    return float((n + 1) * (n + 4) * rsz) if stage == "col_main" else 0.0
+
+
+def fft_flops(n: int) -> float:
+    """Floating-point operations of one length-n transform of the library's
+    FFT (radix-16 stages, then one radix-2/4/8 stage; an FMA counts 2): per
+    point 11 (a radix-16 butterfly set costs 176 per 16 points), 7 (radix 8),
+    4 (radix 4) or 2 (radix 2) per stage, plus in every stage after the first
+    (RAD - 1)/RAD complex twiddle products of 6 each."""
+    lg = n.bit_length() - 1
+    radices = [16] * (lg // 4) + ([1 << (lg % 4)] if lg % 4 else [])
+    per = {16: 11.0, 8: 7.0, 4: 4.0, 2: 2.0}
+    f = sum(per[r] + (6.0 * (r - 1) / r if i > 0 else 0.0) for i, r in enumerate(radices))
+    return f * n
+
+
+def kernel_flops(stage: str, n: int, Q: int) -> float:
+    """Floating-point operations of one launch of the three large passes on an
+    n x n grid (transforms by fft_flops plus the pointwise work around them:
+    packing and the odd chain's e^{-2 pi i k/M} products, the multiplier,
+    the spectrum separation or recombination, the output scaling)."""
+    T = fft_flops(n)
+    return float({
+        "row_fwd": n * (8 * n + 2 * T + 4 * (n + 1) + 4 * (Q + 1)),
+        "col_main": (n + 1) * (18 * n + 4 * T),
+        "row_inv": n * (18 * n + 2 * T),
+    }.get(stage, 0.0))
 
 
 def load_peaks():
@@ -251,8 +291,18 @@ def job_value(world: int, units_per_rank: int, t_max: float) -> float:
     return world * units_per_rank / t_max
 
 
+def workload_config(world: int) -> dict:
+    """The workload, identical in both arms (what is solved, not how)."""
+    return {"workload": WORKLOAD_NAME, "n": WL["n"], "L": WL["L"], "P": WL["P"], "n_r": WL["n_r"],
+            "n_theta": WL["n_theta"], "global_batch": world, "parallelism": f"independent solves x{world}",
+            "l2": f"inputs larger than L2: {N_ROT} rotating 134 MB input/output pairs"}
+
+
 def run_reference(args):
-    """The oracle as the reference arm: each step one bounded oracle sample."""
+    """The oracle as the reference arm: each step one oracle solve of the
+    workload or, when the run would not end within about three minutes, a
+    bounded sample of one (I1 plus the direct sums for a fraction of the polar
+    nodes; the solve's time then is an estimate, flagged as such)."""
     world, rank, _ = dist_setup(False)
     if rank != 0:
         return
@@ -260,31 +310,43 @@ def run_reference(args):
 
     n, L = WL["n"], WL["L"]
     rho = synth.density_abs2(n, n, L, L, WL["seed"], WL["count"])
-    # size the per-step sample so that warmup + steps fit in about three minutes
+    # calibrate on a 1/64 node sample, then take the largest node fraction
+    # whose warmup + timed steps fit in about three minutes
     _, _, _, comp = oracle_sample(rho, node_frac=1.0 / 64)
+    sums64 = (comp["type2"] + comp["type1"]) / max(comp["node_frac"], 1e-12)
     budget = 180.0 / max(1, args.steps + args.warmup)
     frac = 1.0 / 64
-    for f in (1.0, 1.0 / 4, 1.0 / 16):
-        if comp["i1"] + (comp["type2"] + comp["type1"]) * 64 * f <= budget:
+    for f in (1.0, 1.0 / 2, 1.0 / 4, 1.0 / 8, 1.0 / 16, 1.0 / 32):
+        if comp["i1"] + sums64 * f <= budget:
             frac = f
             break
     for _ in range(args.warmup):
         oracle_sample(rho, frac)
-    ests = []
-    desc = ""
+    ests, walls = [], []
+    desc, used = "", frac
     for _ in range(args.steps):
-        est, _, desc, _ = oracle_sample(rho, frac)
+        t0 = time.perf_counter()
+        est, _, desc, c = oracle_sample(rho, frac)
+        walls.append(time.perf_counter() - t0)
         ests.append(est)
+        used = c["node_frac"]
     est = float(np.mean(ests))
     value = 1.0 / est
     cores = os.cpu_count()
+    estimated = used < 1.0
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1000.0,
+        "steps": args.steps, "warmup": args.warmup,
+        # the wall time of each step as run (a whole solve, or the sample)
+        "ms_per_step": float(np.mean(walls)) * 1000.0,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "n": n, "L": L},
+        "data": "synthetic", "config": workload_config(world),
+        "estimated": estimated,
+        "value_basis": ("solves/s of whole solves estimated from the sample: 1 / (t(I1) + t(sums) / node "
+                        "fraction)" if estimated else "solves/s of whole solves, measured"),
+        "node_fraction_per_step": used, "ms_per_solve": est * 1000.0,
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": desc},
+                         "sample": desc, "estimated": estimated},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -343,13 +405,107 @@ def batch_bench(dev, max_time, barrier, reps=5):
     return out
 
 
+def timed_solves(plan, ins, outs, steps, barrier, stream, max_time):
+    """`steps` solves of `plan` over the rotating inputs between CUDA events
+    on the launching stream (barrier + synchronize on both sides); returns the
+    slowest rank's seconds."""
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for i in range(steps):
+        plan.solve(ins[i % len(ins)], outs[i % len(outs)])
+    e1.record(stream)
+    barrier()
+    return max_time(e0.elapsed_time(e1) / 1000.0)
+
+
+def profiled_stages(plan, ins, outs, solves, barrier):
+    """Per-kernel CUDA events (the library records them on the launching
+    stream around each kernel) over `solves` extra solves; returns the average
+    ms per launch of each stage.  Events between kernels serialise them (the
+    band chain then runs in line instead of next to the column pass), so this
+    pass is separate from the timed one."""
+    barrier()
+    plan.profile_begin(solves)
+    for i in range(solves):
+        plan.solve(ins[i % len(ins)], outs[i % len(outs)])
+    stage_ms, n_prof = plan.profile_end()
+    barrier()
+    return {k: v / max(1, n_prof) for k, v in stage_ms.items()}, n_prof
+
+
+def cufft_comparison(dev, rho0, n, L, reps, barrier, stream):
+    """cuFFT (through torch.fft) on the I1 work of the same density, for
+    comparison only (the solver does not use it): rho zero-padded to the
+    2n x 2n grid, a real-to-complex 2D FFT, the multiplier m1 = (1 - p)
+    (-k_x^2/|k|^2) on the half spectrum (a precomputed table), the inverse
+    complex-to-real FFT and the n x n restriction.  Timed as the whole chain
+    and as its two FFTs alone; plus one forward 2n x 2n complex-to-complex
+    FFT.  Returns timings and the I1 arrays (FP64 copy) for an accuracy check."""
+    import torch
+
+    M = 2 * n
+    h = 2.0 * L / n
+    sigma = WL["P"] / 6.0
+    wx = 2.0 * np.pi * torch.fft.rfftfreq(M, d=h, dtype=torch.float64, device=dev)[None, :]
+    wy = 2.0 * np.pi * torch.fft.fftfreq(M, d=h, dtype=torch.float64, device=dev)[:, None]
+    s2 = wx * wx + wy * wy
+    m1 = torch.where(s2 > 0, -(wx * wx) / torch.where(s2 > 0, s2, 1.0) * (-torch.expm1(-s2 / sigma ** 2)), 0.0)
+    del s2
+    out = {}
+    i1s = {}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timeit(fn):
+        fn()
+        barrier()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / reps
+
+    for name, rdt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        pad = torch.zeros(M, M, dtype=rdt, device=dev)
+        mt = m1.to(rdt)
+        res = torch.empty(n, n, dtype=torch.float64, device=dev)
+
+        def chain():
+            pad[:n, :n].copy_(rho0)
+            spec = torch.fft.rfft2(pad)
+            spec.mul_(mt)
+            res.copy_(torch.fft.irfft2(spec, s=(M, M))[:n, :n])
+
+        spec0 = torch.fft.rfft2(pad)
+
+        def ffts():
+            torch.fft.irfft2(torch.fft.rfft2(pad), s=(M, M))
+
+        ms_chain = timeit(chain)
+        ms_ffts = timeit(ffts)
+        i1s[name] = res.cpu().numpy()
+        out[name] = {"i1_chain_ms": ms_chain, "rfft2_plus_irfft2_ms": ms_ffts}
+        del pad, mt, spec0
+    c = torch.zeros(M, M, dtype=torch.complex64, device=dev)
+    out["c2c_fwd_fp32_ms"] = timeit(lambda: torch.fft.fft2(c))
+    del c
+    out["what"] = (f"cuFFT via torch.fft on the I1 work of the same density: pad to {M}^2, rfft2, x m1 table "
+                   f"(half spectrum), irfft2, restrict to {n}^2; and one {M}^2 C2C forward FFT (FP32)")
+    return out, i1s
+
+
 def run_ours(args):
     import torch
 
     world, rank, local = dist_setup(True)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_1409_2014_gb300 import Plan
+    from paper_1409_2014_gb300 import Plan, _abi
     from paper_1409_2014_gb300.build import build
     import synth
 
@@ -359,7 +515,6 @@ def run_ours(args):
     rho0 = torch.from_numpy(rho_np).to(dev)
     ins = [rho0.clone() for _ in range(N_ROT)]
     outs = [torch.empty_like(rho0) for _ in range(N_ROT)]
-    del rho0
 
     def barrier():
         if world > 1:
@@ -368,70 +523,62 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def max_over_ranks_dev(v: float) -> float:
+    def max_time(v: float) -> float:
         return max_over_ranks(v, world, dev)
 
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    plan = Plan(n, lx=L, cut_radius=WL["P"], n_r=WL["n_r"], n_theta=WL["n_theta"],
-                precision="mixed", device=dev)
+    mk = dict(lx=L, cut_radius=WL["P"], n_r=WL["n_r"], n_theta=WL["n_theta"], device=dev)
+    plan = Plan(n, precision="mixed", **mk)
     info = plan.info
     stream = torch.cuda.current_stream(dev)
 
     clocks = ClockSampler(local)
     for i in range(args.warmup):
         plan.solve(ins[i % N_ROT], outs[i % N_ROT])
-    barrier()
-    # ---- timed region: K mixed solves; per-kernel CUDA events are recorded live
-    # around the first n_prof of them (events between kernels cost ~3 % per
-    # solve, so not on every one)
-    n_prof_req = min(args.steps, 200)
-    plan.profile_begin(n_prof_req)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # ---- timed region: K mixed solves, nothing else recorded in it
     tw0 = time.time()
-    e0.record(stream)
-    for i in range(args.steps):
-        plan.solve(ins[i % N_ROT], outs[i % N_ROT])
-    e1.record(stream)
-    barrier()
+    t_max = timed_solves(plan, ins, outs, args.steps, barrier, stream, max_time)
     tw1 = time.time()
-    ms_total = e0.elapsed_time(e1)
-    stage_ms, n_prof = plan.profile_end()
-    n_stages = len(stage_ms)
     clk = clocks.summary(tw0, tw1)
     clocks.stop()
-    t_max = max_over_ranks_dev(ms_total / 1000.0)
     value = job_value(world, args.steps, t_max)
     ms_per_step = t_max * 1000.0 / args.steps
+    n_stages = _abi.dsnu_stage_count()
     if args.only_timed:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s",
-                              "ms_per_step": ms_per_step, "steps": args.steps,
-                              "stages_ms_total": stage_ms, "only_timed": True}), flush=True)
+                              "ms_per_step": ms_per_step, "steps": args.steps, "only_timed": True}), flush=True)
         plan.close()
         return
 
-    # ---- FP64 solver on the same GPU (same input), timed separately
-    plan64 = Plan(n, lx=L, cut_radius=WL["P"], n_r=WL["n_r"], n_theta=WL["n_theta"],
-                  precision="fp64", device=dev)
+    # ---- per-kernel durations: a separate profiled pass of the same solves
+    n_prof_req = max(10, min(args.steps, 200))
+    avg, n_prof = profiled_stages(plan, ins, outs, n_prof_req, barrier)
+    status = {"mixed": plan.status_poll()}
+
+    # ---- the FP32-sum form of the final accumulation (dsnu_accumulation), same input
+    plan_w = Plan(n, precision="mixed", accumulation="working", **mk)
+    kw = max(3, min(args.steps, 200))
+    for i in range(2):
+        plan_w.solve(ins[i % N_ROT], outs[i % N_ROT])
+    t_w = timed_solves(plan_w, ins, outs, kw, barrier, stream, max_time)
+    phi_mixed_w = plan_w.solve(ins[0]).cpu().numpy()
+    status["mixed_working_accumulation"] = plan_w.status_poll()
+    plan_w.close()
+
+    # ---- FP64 solver on the same GPU (same input), timed separately, then profiled
+    plan64 = Plan(n, precision="fp64", **mk)
     k64 = max(3, min(args.steps, 50))
     for i in range(2):
         plan64.solve(ins[i % N_ROT], outs[i % N_ROT])
-    barrier()
-    e0.record(stream)
-    for i in range(k64):
-        plan64.solve(ins[i % N_ROT], outs[i % N_ROT])
-    e1.record(stream)
-    barrier()
-    t64 = max_over_ranks_dev(e0.elapsed_time(e1) / 1000.0)
+    t64 = timed_solves(plan64, ins, outs, k64, barrier, stream, max_time)
     value64 = world * k64 / t64
+    avg64, n_prof64 = profiled_stages(plan64, ins, outs, 5, barrier)
 
     # results of both paths on the first input, for the accuracy check
     phi_mixed = plan.solve(ins[0]).cpu().numpy()
     phi_64 = plan64.solve(ins[0]).cpu().numpy()
+    status["fp64"] = plan64.status_poll()
+    info64 = plan64.info
     plan64.close()
 
     # ---- the standard periodic FFT solver (no split, no padding) on the same input
@@ -440,13 +587,7 @@ def run_ours(args):
         ps = Plan(n, lx=L, partition="none", precision=prec, device=dev)
         for i in range(2):
             ps.solve(ins[i % N_ROT], outs[i % N_ROT])
-        barrier()
-        e0.record(stream)
-        for i in range(reps):
-            ps.solve(ins[i % N_ROT], outs[i % N_ROT])
-        e1.record(stream)
-        barrier()
-        ts = max_over_ranks_dev(e0.elapsed_time(e1) / 1000.0)
+        ts = timed_solves(ps, ins, outs, reps, barrier, stream, max_time)
         standard[prec] = {"solves_per_s": world * reps / ts, "ms_per_step": ts * 1000.0 / reps, "steps": reps}
         ps.close()
 
@@ -458,20 +599,31 @@ def run_ours(args):
     ke = max(3, min(args.steps, 100))
     plan.solve_host_stream([rho_h, rho_h], [phi_h, phi_h])
     barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     plan.solve_host_stream([rho_h] * ke, [phi_h] * ke)
     e1.record(stream)
     barrier()
-    te = max_over_ranks_dev(e0.elapsed_time(e1) / 1000.0)
+    te = max_time(e0.elapsed_time(e1) / 1000.0)
     e2e = {"value": world * ke / te, "unit": "solves/s", "h2d_bytes_per_step": int(rho_h.numel() * 8),
            "d2h_bytes_per_step": int(phi_h.numel() * 8), "steps": ke,
            "api": "dsnu_solve_host_stream (pinned host in/out, copies overlapped with solves)"}
     phi_e2e = phi_h.numpy().copy()
     assert np.array_equal(phi_e2e, phi_mixed), "streamed host solve differs from the device solve"
+    status["mixed_after_e2e"] = plan.status_poll()
+    assert all(v == _abi.DSNU_OK for v in status.values()), status
 
-    # ---- roofline of the dominant kernel
+    # ---- cuFFT on the I1 work (comparison only)
+    cufft, cufft_i1 = cufft_comparison(dev, ins[0], n, L, max(3, min(args.steps, 20)), barrier, stream)
+    ours_i1_ms = sum(avg[k] for k in ("row_fwd", "col_main", "row_inv"))
+    cufft["ours_row_fwd_col_main_row_inv_ms"] = ours_i1_ms
+    cufft["ours_whole_solve_ms"] = ms_per_step
+    cufft["note"] = ("ours: the three large passes of one solve (per-kernel events), which also carry the "
+                     "NUFFT's deconvolved row spectra and band values and read/write FP64 rho and Phi")
+
+    # ---- roofline of the dominant kernel (durations from the profiled pass)
     csz, rsz = 8, 4
-    avg = {k: v / max(1, n_prof) for k, v in stage_ms.items()}
     dom = max(avg, key=avg.get)
     peak, peak_src = load_peaks()
     alg = algorithmic_bytes(dom, n, info.band_q, csz, info.n_nodes, info.kernel_width, rsz,
@@ -481,49 +633,88 @@ def run_ours(args):
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                 else "fallback 6.8 TB/s",
                 "unit": "GB/s", "frac": achieved / peak,
-                "algorithmic_bytes_per_launch": alg, "avg_ms": avg[dom],
+                "algorithmic_bytes_per_launch": alg,
+                "plan_table_bytes_per_launch": plan_table_bytes(dom, n, rsz),
+                "avg_ms": avg[dom],
+                "timing": (f"CUDA events on the launching stream around each kernel, in a separate profiled pass "
+                           f"of {n_prof} solves after the timed region (kernels serialised there)"),
                 "traffic": load_traffic(dom, "4096sq_mixed"),
                 "stages_ms": {k: round(v, 5) for k, v in avg.items()},
                 "stage_share": {k: round(v / sum(avg.values()), 4) for k, v in avg.items()},
-                # every kernel: algorithmic bytes / live duration, as a fraction of the measured peak
+                # every kernel: algorithmic bytes / profiled duration, as a fraction of the measured peak
                 "hbm_frac_per_kernel": {
                     k: round(algorithmic_bytes(k, n, info.band_q, csz, info.n_nodes, info.kernel_width, rsz,
                                                info.n_items, info.spread_tile) / (v * 1e-3) / 1e9 / peak, 4)
                     for k, v in avg.items() if v > 0}}
 
+    # ---- FP64 path: bound by its FP64 arithmetic; peak measured by an FMA loop
+    fp64_peak = _abi.dsnu_measure_fma_peak(_abi.DSNU_FP64, stream.cuda_stream)
+    fp32_peak = _abi.dsnu_measure_fma_peak(_abi.DSNU_MIXED, stream.cuda_stream)
+    dom64 = max(avg64, key=avg64.get)
+    fl64 = {k: kernel_flops(k, n, info64.band_q) for k in ("row_fwd", "col_main", "row_inv")}
+    roof64 = {"bound": "fp64_alu", "kernel": dom64, "achieved": fl64[dom64] / (avg64[dom64] * 1e-3) / 1e12,
+              "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": fl64[dom64] / (avg64[dom64] * 1e-3) / fp64_peak,
+              "flops_per_launch": fl64[dom64], "avg_ms": avg64[dom64],
+              "peak_source": "measured: dsnu_measure_fma_peak(DSNU_FP64), an FP64 FMA loop timed with CUDA events",
+              "flop_count": "the library's radix-16 FFT (fft_flops) plus the pointwise work around it",
+              "fp64_frac_per_kernel": {k: round(fl64[k] / (avg64[k] * 1e-3) / fp64_peak, 4) for k in fl64},
+              "hbm_frac_per_kernel": {
+                  k: round(algorithmic_bytes(k, n, info64.band_q, 16, info64.n_nodes, info64.kernel_width, 8,
+                                             info64.n_items, info64.spread_tile) / (v * 1e-3) / 1e9 / peak, 4)
+                  for k, v in avg64.items() if v > 0},
+              "stages_ms": {k: round(v, 4) for k, v in avg64.items()}, "profiled_solves": n_prof64}
+    fp32_alu = {k: round(kernel_flops(k, n, info.band_q) / (avg[k] * 1e-3) / fp32_peak, 4)
+                for k in ("row_fwd", "col_main", "row_inv")}
+
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "n": n, "L": L, "P": WL["P"], "n_r": WL["n_r"],
-                   "n_theta": WL["n_theta"], "kernel_width": info.kernel_width, "band_q": info.band_q,
-                   "spread_tile_split_chunk": [info.spread_tile, info.spread_split, info.spread_chunk],
-                   "global_batch": world, "parallelism": f"independent solves x{world}",
-                   "l2": f"inputs larger than L2: {N_ROT} rotating 134 MB input/output pairs"},
+        "config": workload_config(world),
+        "plan": {"kernel_width": info.kernel_width, "band_q": info.band_q,
+                 "spread_tile_split_chunk": [info.spread_tile, info.spread_split, info.spread_chunk],
+                 "accumulation": "fp64 (Phi = I1 + I2 added in FP64)"},
         "fp64": {"value": value64, "unit": "solves/s", "ms_per_step": t64 * 1000.0 / k64, "steps": k64,
-                 "dtype": "f64", "mixed_speedup": value / value64},
+                 "dtype": "f64", "mixed_speedup": value / value64, "roofline": roof64},
+        "accumulation": {
+            "fp64": {"solves_per_s": value, "ms_per_step": ms_per_step},
+            "working": {"solves_per_s": world * kw / t_w, "ms_per_step": t_w * 1000.0 / kw, "steps": kw},
+            "fp64_cost_us_per_solve": (ms_per_step - t_w * 1000.0 / kw) * 1000.0},
         "roofline": roofline,
+        "alu": {"fp32_fma_peak_tflops": fp32_peak / 1e12, "fp64_fma_peak_tflops": fp64_peak / 1e12,
+                "fp32_frac_per_kernel": fp32_alu,
+                "note": "flops of the library's FFT algorithm (fft_flops, kernel_flops) / profiled duration"},
         "standard_fft": {"what": "standard periodic FFT solver (kappa = 1, p = 0), same grid and input",
                          **standard},
+        "cufft_comparison": cufft,
         "e2e": e2e,
         "gpu_launches": args.steps * n_stages,
+        "device_status": {k: _abi.STATUS_NAMES.get(v, v) for k, v in status.items()},
         "clocks": clk,
     }
 
     if not args.no_batch:
-        line["batch"] = batch_bench(dev, max_over_ranks_dev, barrier)
+        line["batch"] = batch_bench(dev, max_time, barrier)
 
     if rank == 0 and not args.no_cpu_baseline:
-        est, phi_ref, desc, _ = oracle_sample(rho_np, 1.0)
+        est, ref, desc, comp = oracle_sample(rho_np, 1.0)
+        phi_ref = ref["phi"]
         sub = (slice(0, n, SUB), slice(0, n, SUB))
         acc = {}
-        for name, phi in (("mixed", phi_mixed), ("fp64", phi_64)):
-            d = phi[sub] - phi_ref
-            acc[name] = {"rel_linf": float(np.abs(d).max() / np.abs(phi_ref).max()),
-                         "rel_l2": float(np.linalg.norm(d) / np.linalg.norm(phi_ref))}
-        line["accuracy_vs_oracle"] = {"subsample": f"{n // SUB}^2 stride-{SUB}", **acc}
+        for name, phi in (("mixed", phi_mixed), ("mixed_working_accumulation", phi_mixed_w), ("fp64", phi_64)):
+            d = phi - phi_ref
+            ds = d[sub]
+            acc[name] = {"rel_linf": float(np.abs(ds).max() / np.abs(phi_ref[sub]).max()),
+                         "rel_l2": float(np.linalg.norm(ds) / np.linalg.norm(phi_ref[sub])),
+                         "full_grid_rel_linf": float(np.abs(d).max() / np.abs(phi_ref).max()),
+                         "full_grid_rel_l2": float(np.linalg.norm(d) / np.linalg.norm(phi_ref))}
+        line["accuracy_vs_oracle"] = {"subsample": f"{n // SUB}^2 stride-{SUB} (rel_*), full grid (full_grid_*)",
+                                      **acc}
+        line["cufft_comparison"]["i1_rel_linf_vs_oracle"] = {
+            k: float(np.abs(v - ref["i1"]).max() / np.abs(ref["i1"]).max()) for k, v in cufft_i1.items()}
         line["cpu_baseline"] = {"value": 1.0 / est, "unit": "solves/s", "cores": os.cpu_count(),
-                                "kind": "oracle", "sample": desc}
+                                "kind": "oracle", "sample": desc, "estimated": False,
+                                "seconds": {k: round(v, 3) for k, v in comp.items() if k != "node_frac"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -44,7 +44,8 @@ def _work(rank, world, port, q):
     # the reference arm: rank 0 alone runs (a stand-in for the oracle sample)
     # and prints one JSON line; the other ranks return without output
     bench.oracle_sample = lambda rho, node_frac=1.0: (0.5, None, "stand-in sample",
-                                                      {"i1": 0.0, "type2": 0.0, "type1": 0.0})
+                                                      {"i1": 0.0, "type2": 0.0, "type1": 0.0,
+                                                       "node_frac": 1.0})
     args = type("A", (), {"steps": 2, "warmup": 1})()
     buf = io.StringIO()
     with redirect_stdout(buf):
