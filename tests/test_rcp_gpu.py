@@ -20,7 +20,7 @@ def test_rcp_nr_against_ieee_division(tmp_path):
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     exe = str(tmp_path / "rcp_check")
     subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
-                    "-I" + os.path.join(ROOT, "paper_1409_2014_gb300", "csrc"),
+                    "-I" + os.path.join(ROOT, "paper_1409_2014_gb300", "csrc"), "-I" + os.path.join(ROOT, "include"),
                     os.path.join(ROOT, "tests", "cuda", "rcp_check.cu"), "-o", exe], check=True)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
