@@ -324,6 +324,14 @@ dsnu_status dsnu_ds_linear(dsnu_ds_plan plan, void* u_dev, int32_t adjoint, void
 /* rho <- |u|^2 (FP64 [ny][nx], device), the density of eq. DSII_exact_pot. */
 dsnu_status dsnu_ds_abs2(dsnu_ds_plan plan, const void* u_dev, double* rho_dev, void* stream);
 
+/* Vector-Jacobian product of rho = |u|^2 (the last link of the adjoint of
+ * Phi(|u|^2) with respect to u): grad_u = 2 g_rho u for a real loss, in the
+ * d/dRe + i d/dIm convention.  u_dev and grad_dev: the plan's complex type
+ * [ny][nx] (may alias); g_rho_dev: FP64 [ny][nx] (e.g. dsnu_solve_adjoint of
+ * the gradient at Phi).  Errors: DSNU_EINVAL (NULL argument), DSNU_ECUDA. */
+dsnu_status dsnu_ds_abs2_vjp(dsnu_ds_plan plan, const void* u_dev, const double* g_rho_dev, void* grad_dev,
+                             void* stream);
+
 /* Nonlinear flow with the density and Phi frozen over a step (eqs. 2nd_tssp,
  * 2nd_tssp_more): u <- u e^{i tau (2 beta |u|^2 + 4 beta Phi)} in place;
  * phi_dev: FP64 [ny][nx] potential of the current density. */

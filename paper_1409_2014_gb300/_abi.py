@@ -32,7 +32,7 @@ EXPORTED = [
     "dsnu_batch_create", "dsnu_batch_workspace_bytes", "dsnu_batch_bind", "dsnu_batch_capture_graph",
     "dsnu_batch_solve", "dsnu_batch_destroy", "dsnu_radial_nodes", "dsnu_params_auto",
     "dsnu_plan_create_multiplier", "dsnu_stream_staging_bytes", "dsnu_solve_host_stream",
-    "dsnu_measure_fma_peak",
+    "dsnu_measure_fma_peak", "dsnu_ds_abs2_vjp",
 ]
 
 
@@ -143,6 +143,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dsnu_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), vp]
     lib.dsnu_measure_fma_peak.restype = st
     d = ctypes.c_double
+    lib.dsnu_ds_abs2_vjp.argtypes = [vp, vp, vp, vp, vp]
+    lib.dsnu_ds_abs2_vjp.restype = st
     lib.dsnu_ds_plan_create.argtypes = [ctypes.POINTER(dsnu_ds_params), vp, ctypes.POINTER(vp)]
     lib.dsnu_ds_set_linear_step.argtypes = [vp, d, d, vp]
     lib.dsnu_ds_linear.argtypes = [vp, vp, ctypes.c_int32, vp]
@@ -332,6 +334,10 @@ def dsnu_ds_linear(plan: int, u: int, adjoint: int, stream: int = 0) -> None:
 
 def dsnu_ds_abs2(plan: int, u: int, rho: int, stream: int = 0) -> None:
     _check(load().dsnu_ds_abs2(_vp(plan), _vp(u), _vp(rho), _vp(stream)), "dsnu_ds_abs2")
+
+
+def dsnu_ds_abs2_vjp(plan: int, u: int, g_rho: int, grad: int, stream: int = 0) -> None:
+    _check(load().dsnu_ds_abs2_vjp(_vp(plan), _vp(u), _vp(g_rho), _vp(grad), _vp(stream)), "dsnu_ds_abs2_vjp")
 
 
 def dsnu_ds_nonlinear(plan: int, u: int, phi: int, tau: float, beta: float, stream: int = 0) -> None:

@@ -116,6 +116,18 @@ __global__ void k_abs2(const cpx<R>* __restrict__ u, double* __restrict__ rho, s
   }
 }
 
+// Vector-Jacobian product of rho = |u|^2 for a real loss (gradients in the
+// d/dRe + i d/dIm convention): grad_u = 2 g_rho u, g_rho FP64.
+template <typename R>
+__global__ void k_abs2_vjp(const cpx<R>* __restrict__ u, const double* __restrict__ g_rho,
+                           cpx<R>* __restrict__ grad, size_t n) {
+  for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+    const cpx<R> a = u[i];
+    const R g2 = R(2) * from_f64<R>(g_rho[i]);
+    grad[i] = mk<R>(g2 * a.x, g2 * a.y);
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ void sincos_r(R a, R* s, R* c) {
   if constexpr (sizeof(R) == 4) sincosf(a, s, c);
@@ -439,6 +451,20 @@ dsnu_status dsnu_ds_abs2(dsnu_ds_plan plan, const void* u_dev, double* rho_dev, 
     k_abs2<float><<<grid_1d(n), 256, 0, st>>>(static_cast<const cpx<float>*>(u_dev), rho_dev, n);
   else
     k_abs2<double><<<grid_1d(n), 256, 0, st>>>(static_cast<const cpx<double>*>(u_dev), rho_dev, n);
+  return check_launch();
+}
+
+dsnu_status dsnu_ds_abs2_vjp(dsnu_ds_plan plan, const void* u_dev, const double* g_rho_dev, void* grad_dev,
+                             void* stream) {
+  if (!plan || !u_dev || !g_rho_dev || !grad_dev) return ds_fail(DSNU_EINVAL, "NULL argument");
+  const size_t n = size_t(plan->prm.nx) * plan->prm.ny;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (plan->prm.precision == DSNU_MIXED)
+    k_abs2_vjp<float><<<grid_1d(n), 256, 0, st>>>(static_cast<const cpx<float>*>(u_dev), g_rho_dev,
+                                                 static_cast<cpx<float>*>(grad_dev), n);
+  else
+    k_abs2_vjp<double><<<grid_1d(n), 256, 0, st>>>(static_cast<const cpx<double>*>(u_dev), g_rho_dev,
+                                                  static_cast<cpx<double>*>(grad_dev), n);
   return check_launch();
 }
 

@@ -2,6 +2,9 @@
 
 * ``potential(rho, plan)``: Phi = A rho through the C ABI, differentiable; its
   backward is ``dsnu_solve_adjoint`` (the transposed pipeline).
+* ``potential_of_wave(u, ds, plan)``: Phi(|u|^2) as a function of the wave
+  function u, differentiable; its backward is the hand-written adjoint chain
+  A^T (``dsnu_solve_adjoint``) then 2 g u (``dsnu_ds_abs2_vjp``).
 * ``strang_step(u, ...)``: one Strang step of the time-splitting spectral
   method (Sec. 2.3 of the paper, in its symmetric form): half a linear flow,
   a full nonlinear flow with Phi = A |u|^2 frozen, half a linear flow.  Both
@@ -71,6 +74,14 @@ class DSPlan:
         _abi.dsnu_ds_abs2(self._h, u.data_ptr(), rho.data_ptr(), _stream(self.device))
         return rho
 
+    def abs2_vjp(self, u, g_rho):
+        """2 g_rho u: the gradient with respect to u through rho = |u|^2."""
+        self._chk(u)
+        grad = torch.empty_like(u)
+        _abi.dsnu_ds_abs2_vjp(self._h, u.data_ptr(), g_rho.contiguous().data_ptr(), grad.data_ptr(),
+                              _stream(self.device))
+        return grad
+
     def nonlinear_(self, u, phi, tau, beta):
         self._chk(u)
         _abi.dsnu_ds_nonlinear(self._h, u.data_ptr(), phi.data_ptr(), tau, beta, _stream(self.device))
@@ -120,6 +131,26 @@ class PotentialFn(torch.autograd.Function):
 
 def potential(rho, plan: Plan):
     return PotentialFn.apply(rho, plan)
+
+
+class PotentialOfWaveFn(torch.autograd.Function):
+    """Phi = A |u|^2; backward: grad_u = 2 (A^T g) u, both steps in the library's kernels."""
+
+    @staticmethod
+    def forward(ctx, u, ds: DSPlan, plan: Plan):
+        u = u.contiguous()
+        ctx.save_for_backward(u)
+        ctx.ds, ctx.plan = ds, plan
+        return plan.solve(ds.abs2(u))
+
+    @staticmethod
+    def backward(ctx, g):
+        (u,) = ctx.saved_tensors
+        return ctx.ds.abs2_vjp(u, ctx.plan.solve_adjoint(g.contiguous())), None, None
+
+
+def potential_of_wave(u, ds: DSPlan, plan: Plan):
+    return PotentialOfWaveFn.apply(u, ds, plan)
 
 
 # --------------------------------------------------------------------------- DS flows

@@ -289,3 +289,136 @@ def test_table7_moving_lump_standard_fft_solver(L, h, pu, pphi):
 def test_table8_moving_lump_split_solver(L, h, pu, pphi):
     eu, ephi = _lump_errors(L, h, standard=False)
     assert abs(eu / pu - 1.0) <= 0.006 and abs(ephi / pphi - 1.0) <= 0.006, (eu, ephi)
+
+
+# ------------------------------------------------- config 4 at its stated sizes
+# u on 1024^2, [-32, 32)^2, the u-generator of the 4096^2 workload (16 complex
+# Gaussians), P = 8, 64 x 256 polar nodes; loss L = sum w Phi(|u|^2) with
+# seeded Gaussian-random w; gradients through the hand-written adjoint chain
+# (dsnu_solve_adjoint, then dsnu_ds_abs2_vjp).
+
+def _config4(prec):
+    n, L = 1024, 32.0
+    solver, ds = _plans(n, L, prec, P=8.0, n_r=64, n_theta=256, sigma=0.0)
+    u_np = synth.wavefunction_sum(n, n, L, L, seed=3, count=16)
+    w_np = synth.normal_field(n, n, seed=4)
+    return n, L, solver, ds, u_np, w_np
+
+
+def _wave_loss_grad(u, w, ds, solver):
+    from paper_1409_2014_gb300.ds import potential_of_wave
+
+    u = u.detach().clone().requires_grad_(True)
+    loss = (w * potential_of_wave(u, ds, solver)).sum()
+    loss.backward()
+    return float(loss.detach()), u.grad
+
+
+_ADJ_1024 = {}
+
+
+def _oracle_adjoint_1024(w_np):
+    if "a" not in _ADJ_1024:
+        p = OracleParams(nx=1024, ny=1024, lx=32.0, ly=32.0, cut_radius=8.0, n_r=64, n_theta=256)
+        _ADJ_1024["a"] = oracle.solve_adjoint(w_np, p)  # the transposed direct sums on the full grid
+    return _ADJ_1024["a"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_config4_gradient_vs_oracle_transposed_sums_1024(prec):
+    """dL/du = 2 (A^T w) u on the whole 1024^2 grid: complex128 u with FP64
+    plans to <= 1e-12, complex64 u with mixed plans to <= 2e-5 (relative L-inf)."""
+    n, L, solver, ds, u_np, w_np = _config4(prec)
+    _, g = _wave_loss_grad(torch.from_numpy(u_np).to(CDT[prec]).cuda(), torch.from_numpy(w_np).cuda(), ds, solver)
+    ref = 2.0 * _oracle_adjoint_1024(w_np) * u_np.astype(np.complex64 if prec == "mixed" else np.complex128)
+    g = g.to(torch.complex128).cpu().numpy()
+    assert np.abs(g - ref).max() <= TOL[prec] * np.abs(ref).max()
+    solver.close()
+    ds.close()
+
+
+def test_config4_central_differences_16_directions_64_entries():
+    """complex128 on 1024^2, h = 1e-6: 16 seeded random directions and 64
+    single entries (real and imaginary parts of seeded grid points where the
+    gradient is not negligible) against the adjoint's directional derivatives."""
+    from paper_1409_2014_gb300.ds import potential_of_wave
+
+    n, L, solver, ds, u_np, w_np = _config4("fp64")
+    u = torch.from_numpy(u_np).cuda()
+    w = torch.from_numpy(w_np).cuda()
+    _, g = _wave_loss_grad(u, w, ds, solver)
+
+    def L_of(v):
+        with torch.no_grad():
+            return float((w * potential_of_wave(v, ds, solver)).sum())
+
+    h = 1e-6
+    # rounding noise of a loss difference: the two evaluations' rounding errors
+    # (a few ulps per term, random signs) add up like the L2 norm of the terms
+    scale = float(torch.linalg.vector_norm(w * potential_of_wave(u, ds, solver)))
+    noise = 16 * np.finfo(np.float64).eps * scale / h
+    gen = torch.Generator(device="cpu").manual_seed(16)
+    for _ in range(16):
+        d = torch.complex(torch.randn(n, n, generator=gen, dtype=torch.float64),
+                          torch.randn(n, n, generator=gen, dtype=torch.float64)).cuda()
+        fd = (L_of(u + h * d) - L_of(u - h * d)) / (2 * h)
+        an = float((g.real * d.real + g.imag * d.imag).sum())
+        assert abs(fd - an) <= 1e-7 * abs(an) + noise, (fd, an)
+    gmag = g.abs().cpu().numpy()
+    cand = np.flatnonzero(gmag.ravel() > 0.05 * gmag.max())
+    pick = np.random.Generator(np.random.PCG64(64)).choice(cand, size=64, replace=False)
+    for k, idx in enumerate(pick):
+        iy, ix = divmod(int(idx), n)
+        unit = 1.0 if k % 2 == 0 else 1j
+        d = torch.zeros(n, n, dtype=torch.complex128, device="cuda")
+        d[iy, ix] = unit
+        fd = (L_of(u + h * d) - L_of(u - h * d)) / (2 * h)
+        an = float(g[iy, ix].real) if k % 2 == 0 else float(g[iy, ix].imag)
+        assert abs(fd - an) <= 1e-6 * abs(an) + noise, (iy, ix, fd, an)
+    solver.close()
+    ds.close()
+
+
+def test_config4_complex64_gradient_vs_fp64_adjoint_1024():
+    """The complex64 / mixed-precision gradient against the FP64 adjoint
+    (complex128 / FP64 plans) on the same u (FD is meaningless in FP32)."""
+    grads = {}
+    for prec in ("fp64", "mixed"):
+        n, L, solver, ds, u_np, w_np = _config4(prec)
+        _, g = _wave_loss_grad(torch.from_numpy(u_np).to(CDT[prec]).cuda(), torch.from_numpy(w_np).cuda(), ds,
+                               solver)
+        grads[prec] = g.to(torch.complex128).cpu().numpy()
+        solver.close()
+        ds.close()
+    ref = grads["fp64"]
+    assert np.abs(grads["mixed"] - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+def test_config4_200_steps_complex64_checkpointed():
+    """complex64 u on 1024^2, 200 Strang steps (alpha = beta = 1, dt = 1e-3):
+    mass conserved to FP32 rounding, the checkpointed gradient equals the
+    full-tape gradient, and it follows the complex128 gradient."""
+    from paper_1409_2014_gb300.ds import evolve, mass
+
+    steps, tau = 200, 1e-3
+    out_grads = {}
+    for prec in ("mixed", "fp64"):
+        n, L, solver, ds, u_np, w_np = _config4(prec)
+        u0 = torch.from_numpy(u_np).to(CDT[prec]).cuda()
+        w = torch.from_numpy(w_np).cuda()
+        gs = []
+        for ck in ((14, 0) if prec == "mixed" else (14,)):
+            u = u0.clone().requires_grad_(True)
+            out = evolve(u, steps, ds, solver, tau, 1.0, 1.0, checkpoint_every=ck)
+            if prec == "mixed" and ck:
+                m0, m1 = mass(u0.to(torch.complex128), L, L), mass(out.detach().to(torch.complex128), L, L)
+                assert abs(m1 / m0 - 1.0) < 1e-4
+            (w * (out.real.double() ** 2 + out.imag.double() ** 2)).sum().backward()
+            gs.append(u.grad.to(torch.complex128).clone())
+        if prec == "mixed":
+            assert torch.allclose(gs[0], gs[1], rtol=0, atol=1e-5 * float(gs[1].abs().max()))
+        out_grads[prec] = gs[0].cpu().numpy()
+        solver.close()
+        ds.close()
+    ref = out_grads["fp64"]
+    assert np.abs(out_grads["mixed"] - ref).max() <= 1e-3 * np.abs(ref).max()
