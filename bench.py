@@ -49,7 +49,9 @@ def parse():
                     help="skip the oracle run (no accuracy / cpu_baseline keys)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-member batch measurement")
     ap.add_argument("--only-timed", action="store_true",
-                    help="run only warmup + the timed mixed region (for profiler launch lists)")
+                    help="run only warmup + the timed region (for profiler launch lists)")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
+                    help="precision of the timed solves of an --only-timed run")
     return ap.parse_args()
 
 
@@ -121,6 +123,12 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.samples.append((time.time(), [f.strip() for f in line.split(",")]))
 
+    def wait_first(self, timeout: float = 5.0):
+        """Block until nvidia-smi has printed its first sample (or timeout)."""
+        t_end = time.time() + timeout
+        while self.proc is not None and not self.samples and time.time() < t_end:
+            time.sleep(0.02)
+
     def stop(self):
         if self.proc is not None:
             self.proc.terminate()
@@ -132,6 +140,9 @@ class ClockSampler:
     def summary(self, t0: float, t1: float):
         win = [s for t, s in self.samples if t0 <= t <= t1 and len(s) >= 9]
         where = "timed region"
+        if not win:  # a timed region shorter than the sampling interval
+            win = [s for t, s in self.samples if t0 - 0.5 <= t <= t1 + 0.5 and len(s) >= 9]
+            where = "timed region +- 0.5 s (the region is shorter than the 50 ms sampling interval)"
         if not win:
             win = [s for _, s in self.samples if len(s) >= 9]
             where = "whole run (no sample fell inside the timed region)"
@@ -527,11 +538,12 @@ def run_ours(args):
         return max_over_ranks(v, world, dev)
 
     mk = dict(lx=L, cut_radius=WL["P"], n_r=WL["n_r"], n_theta=WL["n_theta"], device=dev)
-    plan = Plan(n, precision="mixed", **mk)
+    plan = Plan(n, precision=args.precision if args.only_timed else "mixed", **mk)
     info = plan.info
     stream = torch.cuda.current_stream(dev)
 
     clocks = ClockSampler(local)
+    clocks.wait_first()
     for i in range(args.warmup):
         plan.solve(ins[i % N_ROT], outs[i % N_ROT])
     # ---- timed region: K mixed solves, nothing else recorded in it
