@@ -252,8 +252,9 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def load_traffic(stage: str, workload: str):
-    """ncu dram bytes per launch recorded for this kernel source, else None."""
+def load_traffic(stage: str, workload: str, field: str = "dram_bytes_per_launch"):
+    """A counter recorded by ncu for this kernel source (default: DRAM bytes
+    per launch), else None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             tab = json.load(fh)
@@ -262,7 +263,7 @@ def load_traffic(stage: str, workload: str):
     ent = tab.get(f"{stage}|{workload}")
     if not ent or ent.get("kernel_hash") != kernel_hash():
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent.get(field)
 
 
 # --------------------------------------------------------------------------- arms
@@ -669,6 +670,9 @@ def run_ours(args):
               "flops_per_launch": fl64[dom64], "avg_ms": avg64[dom64],
               "peak_source": "measured: dsnu_measure_fma_peak(DSNU_FP64), an FP64 FMA loop timed with CUDA events",
               "flop_count": "the library's radix-16 FFT (fft_flops) plus the pointwise work around it",
+              "traffic": load_traffic(dom64, "4096sq_fp64"),
+              "ncu_fp64_pipe_active_pct": {k: load_traffic(k, "4096sq_fp64", "fp64_pipe_active_pct")
+                                           for k in ("row_fwd", "col_main", "row_inv")},
               "fp64_frac_per_kernel": {k: round(fl64[k] / (avg64[k] * 1e-3) / fp64_peak, 4) for k in fl64},
               "hbm_frac_per_kernel": {
                   k: round(algorithmic_bytes(k, n, info64.band_q, 16, info64.n_nodes, info64.kernel_width, 8,
