@@ -364,10 +364,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def batch_bench(dev, max_time, barrier, reps=5):
+def batch_bench(dev, max_time, barrier, reps=20):
     """64 seeded densities (4-16 Gaussians) with grids drawn from {256, 512,
     1024, 2048}^2 on [-32,32)^2, P = 8, 64 x 256 nodes: mixed plans in one
-    batch replayed as a CUDA graph, versus 64 separate FP64 solves."""
+    batch replayed as a CUDA graph (the default schedule, one launch sequence
+    per grid size on forked streams, and one launch per pipeline stage for all
+    grid sizes), versus 64 separate FP64 solves."""
     import torch
 
     import synth
@@ -387,18 +389,23 @@ def batch_bench(dev, max_time, barrier, reps=5):
         plans = {n: Plan(n, lx=32.0, cut_radius=8.0, n_r=64, n_theta=256, precision=prec, device=dev)
                  for n in sizes}
         if prec == "mixed":
-            b = Batch([plans[m[0]] for m in members], rhos, phis)
-            b.capture_graph()
-            b.solve()
-            barrier()
-            e0.record(stream)
-            for _ in range(reps):
+            # the two schedules of the same batch: one launch sequence per grid size on
+            # forked streams (the default), and one launch per pipeline stage for all sizes
+            for key, sched in (("mixed_graph_batch", "auto"),
+                               ("mixed_graph_batch_stage_launches", "stage_launches")):
+                b = Batch([plans[m[0]] for m in members], rhos, phis, schedule=sched)
+                b.capture_graph()
                 b.solve()
-            e1.record(stream)
-            barrier()
-            t = max_time(e0.elapsed_time(e1) / 1000.0)
-            out["mixed_graph_batch"] = {"solves_per_s": reps * len(members) / t, "ms_per_batch": 1e3 * t / reps}
-            b.close()
+                barrier()
+                e0.record(stream)
+                for _ in range(reps):
+                    b.solve()
+                e1.record(stream)
+                barrier()
+                t = max_time(e0.elapsed_time(e1) / 1000.0)
+                out[key] = {"solves_per_s": reps * len(members) / t, "ms_per_batch": 1e3 * t / reps,
+                            "schedule": b.schedule_in_use, "launches_per_batch": b.launches}
+                b.close()
         else:
             for (n, _, _), r, f in zip(members, rhos, phis):
                 plans[n].solve(r, f)

@@ -357,11 +357,31 @@ dsnu_status dsnu_ds_plan_destroy(dsnu_ds_plan plan);
 /* ---------------------------------------------------------------------------
  * Batches: many densities, possibly on different grids, per launch sequence.
  * Members that share a plan are solved together (each kernel runs once for the
- * group, its CTAs iterating over members and work items); distinct plans run
- * on forked streams.  Results are bitwise identical to one dsnu_solve per
- * member.
+ * group, its CTAs iterating over members and work items).  Distinct plans are
+ * scheduled in one of two ways (dsnu_batch_set_schedule):
+ *   - one launch per pipeline stage for all plans, eight launches per batch
+ *     solve, each plan's members on their own range of the stage's persistent
+ *     CTAs, the band chain on a plan-owned side stream next to the column
+ *     stage (mixed-precision split plans with the DS multiplier, grids of 256
+ *     to 2048 points per axis, at most 8 distinct plans; when the plans'
+ *     spreading autotuners chose different tiles, the two spreading kernels
+ *     run once per plan instead);
+ *   - one launch sequence per distinct plan on forked streams (any plans).
+ * With forked streams every member's result is bitwise identical to its own
+ * dsnu_solve (the same kernels).  The stage launches run the same kernel
+ * bodies compiled into other kernels, where the compiler may contract
+ * multiply-adds differently: results equal the member's dsnu_solve to FP32
+ * rounding, and repeated batch solves are bitwise reproducible.
  * ------------------------------------------------------------------------- */
 typedef struct dsnu_batch_s* dsnu_batch;
+
+typedef enum {
+  DSNU_BATCH_AUTO = 0,            /* the faster for this GPU: forked streams (measured on GB300: the 64-member
+                                     batch of 256^2 .. 2048^2 grids in 3.26 ms, against 3.43 ms with one
+                                     launch per stage, whose stages end for all grid sizes at once) */
+  DSNU_BATCH_STAGE_LAUNCHES = 1,  /* one launch per stage (DSNU_EUNSUPPORTED when the plans do not allow it) */
+  DSNU_BATCH_FORKED_STREAMS = 2   /* one launch sequence per distinct plan on forked streams */
+} dsnu_batch_schedule_kind;
 
 /* count members; plans[i] is member i's plan (plans may repeat).  The batch
  * keeps the plan handles: they must outlive it.  Creates one stream and one
@@ -376,20 +396,41 @@ size_t dsnu_batch_workspace_bytes(dsnu_batch b);
 /* Bind the members' device buffers: rho_dev[i] (FP64 [ny_i][nx_i], read) and
  * phi_dev[i] (written), both 16-byte aligned, and the caller-owned batch workspace (>=
  * dsnu_batch_workspace_bytes, 256-byte aligned).  Uploads the member tables
- * on `stream` and synchronises it; drops a previously captured graph.
- * Errors: DSNU_EINVAL, DSNU_ECUDA. */
+ * on `stream` and synchronises it (and builds the host table of the
+ * one-launch-per-stage schedule when it is used); drops a previously captured
+ * graph.
+ * Errors: DSNU_EINVAL, DSNU_EUNSUPPORTED (DSNU_BATCH_STAGE_LAUNCHES was asked
+ * for plans that do not allow it), DSNU_ECUDA. */
 dsnu_status dsnu_batch_bind(dsnu_batch b, const double* const* rho_dev, double* const* phi_dev,
                             void* workspace_dev, size_t bytes, void* stream);
 
-/* Capture the batch's launch sequence (all groups, forked streams joined back
- * to `stream`) into a CUDA graph, instantiated once; dsnu_batch_solve then
- * replays it.  `stream` must not be capturing already. */
+/* Choose how the batch's distinct plans are scheduled (dsnu_batch_schedule_kind;
+ * a new batch uses DSNU_BATCH_AUTO).  Host only: once the batch is bound, the
+ * one-launch-per-stage schedule's table (CTA ranges per plan and stage, the
+ * plans' table pointers) is built in host memory and passed by value to the
+ * stage launches.  Drops a previously captured graph.
+ * Errors: DSNU_EINVAL (NULL batch, unknown schedule), DSNU_EUNSUPPORTED
+ * (DSNU_BATCH_STAGE_LAUNCHES for plans that do not allow it; the previous
+ * schedule stays), DSNU_ECUDA. */
+dsnu_status dsnu_batch_set_schedule(dsnu_batch b, int32_t schedule);
+
+/* The schedule in use (DSNU_BATCH_STAGE_LAUNCHES or DSNU_BATCH_FORKED_STREAMS),
+ * and the number of kernel launches of one batch solve; -1 before
+ * dsnu_batch_bind or for a NULL batch. */
+int32_t dsnu_batch_schedule(dsnu_batch b);
+int32_t dsnu_batch_launches(dsnu_batch b);
+
+/* Capture the batch's launch sequence (the stage launches, or all groups'
+ * sequences with the forked streams joined back to `stream`) into a CUDA
+ * graph, instantiated once; dsnu_batch_solve then replays it.  `stream` must
+ * not be capturing already. */
 dsnu_status dsnu_batch_capture_graph(dsnu_batch b, void* stream);
 
 /* Solve every member: graph replay when captured, else the launches.  Only
  * launches (no allocation, no synchronisation). */
 dsnu_status dsnu_batch_solve(dsnu_batch b, void* stream);
 
+/* Free the batch (no solve of it may be in flight).  NULL is accepted. */
 dsnu_status dsnu_batch_destroy(dsnu_batch b);
 
 /* Plan introspection for tests and benchmarks (host values, no device work). */

@@ -193,14 +193,21 @@ class Plan:
             pass
 
 
+_SCHEDULE = {"auto": _abi.DSNU_BATCH_AUTO, "stage_launches": _abi.DSNU_BATCH_STAGE_LAUNCHES,
+             "forked_streams": _abi.DSNU_BATCH_FORKED_STREAMS}
+
+
 class Batch:
     """Many densities per launch sequence (members may use different plans).
 
     ``Batch(plans, rhos, phis)`` binds device tensors; ``solve()`` runs every
     member; ``capture_graph()`` records the launch sequence as a CUDA graph
-    that ``solve()`` then replays."""
+    that ``solve()`` then replays.  ``schedule``: "stage_launches" (one launch
+    per pipeline stage for all grid sizes), "forked_streams" (one launch
+    sequence per plan on forked streams) or "auto" (the faster on this GPU:
+    forked streams); ``schedule_in_use`` and ``launches`` report the result."""
 
-    def __init__(self, plans, rhos, phis):
+    def __init__(self, plans, rhos, phis, schedule="auto"):
         import torch
 
         if not (len(plans) == len(rhos) == len(phis)) or not plans:
@@ -211,11 +218,22 @@ class Batch:
         self.plans, self.rhos, self.phis = list(plans), list(rhos), list(phis)
         self.device = plans[0].device
         self._h = _abi.dsnu_batch_create([p.handle for p in plans])
+        _abi.dsnu_batch_set_schedule(self._h, _SCHEDULE[schedule])
         nbytes = _abi.dsnu_batch_workspace_bytes(self._h)
         self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
         _abi.dsnu_batch_bind(self._h, [r.data_ptr() for r in rhos], [f.data_ptr() for f in phis],
                              self.workspace.data_ptr(), self.workspace.numel(),
                              torch.cuda.current_stream(self.device).cuda_stream)
+
+    @property
+    def schedule_in_use(self) -> str:
+        return {_abi.DSNU_BATCH_STAGE_LAUNCHES: "stage_launches",
+                _abi.DSNU_BATCH_FORKED_STREAMS: "forked_streams"}[_abi.dsnu_batch_schedule(self._h)]
+
+    @property
+    def launches(self) -> int:
+        """Kernel launches of one batch solve."""
+        return _abi.dsnu_batch_launches(self._h)
 
     def capture_graph(self):
         import torch

@@ -18,6 +18,7 @@ DSNU_FP64, DSNU_MIXED = 0, 1
 DSNU_PARTITION_GAUSS, DSNU_PARTITION_SHARP, DSNU_PARTITION_NONE = 0, 1, 2
 DSNU_RADIAL_LEGENDRE, DSNU_RADIAL_JACOBI = 0, 1
 DSNU_ACCUM_FP64, DSNU_ACCUM_WORKING = 0, 1
+DSNU_BATCH_AUTO, DSNU_BATCH_STAGE_LAUNCHES, DSNU_BATCH_FORKED_STREAMS = 0, 1, 2
 
 STATUS_NAMES = {0: "DSNU_OK", 1: "DSNU_EINVAL", 2: "DSNU_ENOMEM", 3: "DSNU_ECUDA",
                 4: "DSNU_ETIMEOUT", 5: "DSNU_EUNSUPPORTED"}
@@ -32,7 +33,8 @@ EXPORTED = [
     "dsnu_batch_create", "dsnu_batch_workspace_bytes", "dsnu_batch_bind", "dsnu_batch_capture_graph",
     "dsnu_batch_solve", "dsnu_batch_destroy", "dsnu_radial_nodes", "dsnu_params_auto",
     "dsnu_plan_create_multiplier", "dsnu_stream_staging_bytes", "dsnu_solve_host_stream",
-    "dsnu_measure_fma_peak", "dsnu_ds_abs2_vjp",
+    "dsnu_measure_fma_peak", "dsnu_ds_abs2_vjp", "dsnu_batch_set_schedule", "dsnu_batch_schedule",
+    "dsnu_batch_launches",
 ]
 
 
@@ -143,6 +145,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dsnu_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), vp]
     lib.dsnu_measure_fma_peak.restype = st
     d = ctypes.c_double
+    lib.dsnu_batch_set_schedule.argtypes = [vp, ctypes.c_int32]
+    lib.dsnu_batch_set_schedule.restype = st
+    lib.dsnu_batch_schedule.argtypes = [vp]
+    lib.dsnu_batch_schedule.restype = ctypes.c_int32
+    lib.dsnu_batch_launches.argtypes = [vp]
+    lib.dsnu_batch_launches.restype = ctypes.c_int32
     lib.dsnu_ds_abs2_vjp.argtypes = [vp, vp, vp, vp, vp]
     lib.dsnu_ds_abs2_vjp.restype = st
     lib.dsnu_ds_plan_create.argtypes = [ctypes.POINTER(dsnu_ds_params), vp, ctypes.POINTER(vp)]
@@ -375,6 +383,18 @@ def dsnu_batch_bind(batch: int, rho_ptrs, phi_ptrs, ws: int, nbytes: int, stream
     r = (ctypes.c_void_p * len(rho_ptrs))(*rho_ptrs)
     p = (ctypes.c_void_p * len(phi_ptrs))(*phi_ptrs)
     _check(load().dsnu_batch_bind(_vp(batch), r, p, _vp(ws), nbytes, _vp(stream)), "dsnu_batch_bind")
+
+
+def dsnu_batch_set_schedule(batch: int, schedule: int) -> None:
+    _check(load().dsnu_batch_set_schedule(_vp(batch), ctypes.c_int32(schedule)), "dsnu_batch_set_schedule")
+
+
+def dsnu_batch_schedule(batch: int) -> int:
+    return int(load().dsnu_batch_schedule(_vp(batch)))
+
+
+def dsnu_batch_launches(batch: int) -> int:
+    return int(load().dsnu_batch_launches(_vp(batch)))
 
 
 def dsnu_batch_capture_graph(batch: int, stream: int = 0) -> None:

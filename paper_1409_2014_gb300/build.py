@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdsnufft.so")
 
-SOURCES = ["plan.cu", "pipeline_f32.cu", "pipeline_f64.cu", "noalloc.cu", "ds.cu", "batch.cu", "measure.cu"]
+SOURCES = ["plan.cu", "pipeline_f32.cu", "pipeline_f64.cu", "noalloc.cu", "ds.cu", "batch.cu", "batch_ragged.cu",
+           "measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -132,6 +132,24 @@ inline Members single_member(const double* rho, double* phi, void* ws) {
 cudaError_t prepare_kernels_f32(PlanGeom& g);
 cudaError_t prepare_kernels_f64(PlanGeom& g);
 
+// A batch's plans solved by one launch per pipeline stage (batch_ragged.cu):
+// one entry per distinct plan with its members' device table.
+constexpr int kRagMaxGroups = 8;
+struct RaggedGroupIn {
+  dsnu_plan plan;
+  const Member* dev_members;  // count members (device)
+  Member first;               // the first of them (for one-member groups)
+  int count;
+};
+struct Ragged;
+// Whether these plans can share stage launches (why not, in *why).
+bool ragged_eligible(const dsnu_plan* plans, int n, std::string* why);
+// Build the stage table (host memory; the stage launches pass it by value).
+dsnu_status ragged_create(const RaggedGroupIn* groups, int n, Ragged** out);
+dsnu_status ragged_enqueue(const Ragged* r, cudaStream_t st);
+int ragged_launches(const Ragged* r);  // kernel launches per batch solve
+void ragged_destroy(Ragged* r);
+
 void set_last_error(const std::string& msg);
 
 }  // namespace dsnu

@@ -40,9 +40,8 @@
 #include "common.cuh"
 #include "internal.h"
 
-// Occupancy targets (minimum resident CTAs per SM), rows per CTA of the FP32
-// row passes and the column-pass variant (both chains paired in registers, or
-// one chain at a time); overridable at compile time for tuning sweeps.
+// Occupancy targets (minimum resident CTAs per SM) and rows per CTA of the
+// FP32 row passes; overridable at compile time for tuning sweeps.
 #ifndef DSNU_ROW_MINB
 #define DSNU_ROW_MINB 2
 #endif
@@ -54,9 +53,6 @@
 #endif
 #ifndef DSNU_ROWI_RB32
 #define DSNU_ROWI_RB32 2
-#endif
-#ifndef DSNU_COL_PAIRED
-#define DSNU_COL_PAIRED 1
 #endif
 // Forward row pass: bulk prefetch of the next rows of rho (FP32 plans), with
 // the landing rows N + DSNU_ROWF_LPAD doubles apart
@@ -275,7 +271,10 @@ struct Geo {
 
 // Every FFT kernel is persistent: a grid of at most (SMs x resident CTAs)
 // loops over its work items (row blocks or column blocks) and keeps the FFT
-// stage twiddles in shared memory for the whole launch.
+// stage twiddles in shared memory for the whole launch.  Each kernel's body is
+// a device function of the CTA's index vb among vg CTAs that share the work,
+// so that one launch can also serve several plans, each on its own range of
+// CTAs (batch_ragged.cu).
 
 // ---------------------------------------------------------------------------
 // Forward row pass: per row, the even and odd output frequencies of the
@@ -283,9 +282,9 @@ struct Geo {
 // interleaved length-N transforms of z and z w_M^n), then the two real-signal
 // spectra are separated at every q in [0, N].
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RF, min_blocks<R>(Geo<R, LOG2N>::MINB_F))
-k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
-          const R* __restrict__ decon_y, int cj, int* status) {
+__device__ __forceinline__ void row_fwd_body(int vb, int vg, Members mem, WsOff off, int ldqA, int ldqB, int Q,
+                                             int ny, AxisTabs<R> ax, const R* __restrict__ decon_y, int cj,
+                                             int* status) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, RB = GG::RB_F, T = GG::T_RF, RS = GG::RS;
   constexpr bool PF = GG::ROW_PF;
@@ -324,11 +323,11 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
       bulk_load(land + r * GG::LS, src + size_t(r) * N, unsigned(N * sizeof(double)), bar, pol);
   };
   if constexpr (PF)
-    if (tid == 0 && int(blockIdx.x) < total) prefetch(blockIdx.x);
+    if (tid == 0 && vb < total) prefetch(vb);
   unsigned phase = 0;
 #pragma unroll 1
-  for (int it = blockIdx.x; it < total; it += gridDim.x) {
-    if (it + int(gridDim.x) >= total) grid_dep_trigger();  // last item of this CTA
+  for (int it = vb; it < total; it += vg) {
+    if (it + vg >= total) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     const Member mb = member_at(mem, mi);
     const double* __restrict__ rho = mb.rho;
@@ -369,7 +368,7 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     if constexpr (PF) {
       // every thread has read the landing buffer (a barrier); stop if a wait expired
       if (cta_timed_out(landed, bar, phase ^ 1u, status)) return;
-      if (tid == 0 && it + int(gridDim.x) < total) prefetch(it + gridDim.x);
+      if (tid == 0 && it + vg < total) prefetch(it + vg);
     }
     block_fft2_regs<R, LOG2N, PF>(e, o, buf_e, buf_o, t, stw, cj != 0);
     __syncthreads();  // last-stage loads (and the previous unpack) finished
@@ -416,15 +415,21 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
   }
 }
 
-#if DSNU_COL_PAIRED
+template <typename R, int LOG2N>
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RF, min_blocks<R>(Geo<R, LOG2N>::MINB_F))
+k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
+          const R* __restrict__ decon_y, int cj, int* status) {
+  row_fwd_body<R, LOG2N>(blockIdx.x, gridDim.x, mem, off, ldqA, ldqB, Q, ny, ax, decon_y, cj, status);
+}
+
 // ---------------------------------------------------------------------------
 // Column pass of I1: per column, both chains (even/odd output rows of the
 // padded column DFT) go forward together, are multiplied by m1 and come back
 // together; their sum is the column of I1's inverse.  All loads of a column
 // precede the first barrier, so the in-place update is safe.
 template <typename R, int LOG2N, bool GEN>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COLMAIN_MINB))
-k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs<R> mt, int cj) {
+__device__ __forceinline__ void col_main_body(int vb, int vg, Members mem, WsOff off, int ldqA, int ncols,
+                                              AxisTabs<R> ay, MultTabs<R> mt, int cj) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, CC = GG::CC, FB = GG::FB;
   // FP32 with the DS multiplier: the e^{-2 pi i n/M} factors of the odd chain
@@ -462,7 +467,7 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
   };
   if constexpr (TAB) {
     for (int i = tid; i < N; i += GG::T_C) wtab[i] = twm(ay, i);
-    if (int(blockIdx.x) < total) fetch_mult(blockIdx.x, 0);  // (a plan table: no wait needed)
+    if (vb < total) fetch_mult(vb, 0);  // (a plan table: no wait needed)
     __syncthreads();
   }
   grid_dep_wait();
@@ -479,11 +484,11 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
       x[m] = (col2 < ncols) ? A2[Tile<R>::at(t + G * m, col2, ldqA)] : mk<R>(R(0), R(0));
   };
   if constexpr (PF)
-    if (int(blockIdx.x) < total) load_col(blockIdx.x, xn);
+    if (vb < total) load_col(vb, xn);
   int kk = 0;  // items done by this CTA (the multiplier buffer is kk & 1)
 #pragma unroll 1
-  for (int it = blockIdx.x; it < total; it += gridDim.x, ++kk) {
-    if (it + int(gridDim.x) >= total) grid_dep_trigger();  // last item of this CTA
+  for (int it = vb; it < total; it += vg, ++kk) {
+    if (it + vg >= total) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(member_at(mem, mi), off.A);
     const int col = item * CC + cl;
@@ -541,11 +546,11 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
       }
     }
     if constexpr (PF)
-      if (it + int(gridDim.x) < total) load_col(it + gridDim.x, xn);
+      if (it + vg < total) load_col(it + vg, xn);
     // the next item's m1 rows into the other buffer (last read by the item
     // before this one, whose reads the barriers since then have completed)
     if constexpr (TAB)
-      if (it + int(gridDim.x) < total) fetch_mult(it + gridDim.x, (kk + 1) & 1);
+      if (it + vg < total) fetch_mult(it + vg, (kk + 1) & 1);
     block_fft2_regs<R, LOG2N>(e, o, buf_e, buf_o, t, stw, cj == 0);
     if (valid) {
 #pragma unroll
@@ -560,83 +565,19 @@ k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs
   }
 }
 
-#else
-// ---------------------------------------------------------------------------
-// Column pass of I1, one chain at a time: the even chain's result is held in
-// shared memory until the odd one is done (fewer registers than the paired
-// variant).  The odd
-// chain's loads of a column precede its first barrier, so the in-place update
-// is safe.
 template <typename R, int LOG2N, bool GEN>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COLMAIN_MINB))
 k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs<R> mt, int cj) {
-  using GG = Geo<R, LOG2N>;
-  constexpr int N = GG::N, G = GG::G, CC = GG::CC, FB = GG::FB;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<R>* stw = reinterpret_cast<cpx<R>*>(smem_raw);
-  cpx<R>* sm = stw + GG::STWP;
-  copy_to_smem(stw, ay.stw, GG::STW);
-  const int tid = threadIdx.x;
-  const int cl = tid / G, t = tid - cl * G;
-  const R isg = cj ? R(-1) : R(1);
-  cpx<R>* buf = sm + cl * FB;
-  cpx<R>* held = sm + CC * FB + cl * N;  // even-chain result, index n
-  grid_dep_wait();
-  const int items = (ncols + CC - 1) / CC;
-#pragma unroll 1
-  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
-    const int mi = it / items, item = it - mi * items;
-    cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(member_at(mem, mi), off.A);
-    const int col = item * CC + cl;
-    const bool valid = col < ncols;
-    const R wx2 = valid ? mt.wx2[col] : R(0);
-    const R gx = valid ? mt.gx[col] : R(0);
-    const R kxc = (GEN && valid) ? mt.kx[col] : R(0);
-#pragma unroll 1
-    for (int par = 0; par < 2; ++par) {
-      cpx<R> v[16];
-#pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        const int n = t + G * m;
-        cpx<R> x = valid ? A[Tile<R>::at(n, col, ldqA)] : mk<R>(R(0), R(0));
-        if (par) {
-          cpx<R> w = twm(ay, n);
-          w.y *= isg;
-          x = cmul(x, w);
-        }
-        v[m] = x;
-      }
-      block_fft_regs<R, LOG2N>(v, buf, t, stw, cj != 0);
-#pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        const int q = 2 * (t + G * m) + par;
-        v[m] = v[m] * (valid ? mult_high<GEN>(mt, wx2, kxc, gx, q) : R(0));
-      }
-      block_fft_regs<R, LOG2N>(v, buf, t, stw, cj == 0);
-      if (par == 0) {
-#pragma unroll
-        for (int m = 0; m < 16; ++m) held[t + G * m] = v[m];
-      } else if (valid) {
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          const int n = t + G * m;
-          const cpx<R> w = twm(ay, n);
-          const cpx<R> e = held[n];
-          A[Tile<R>::at(n, col, ldqA)] = cj ? e + cmul(v[m], w) : e + cmulc(v[m], w);
-        }
-      }
-    }
-  }
+  col_main_body<R, LOG2N, GEN>(blockIdx.x, gridDim.x, mem, off, ldqA, ncols, ay, mt, cj);
 }
 
-#endif
 
 // ---------------------------------------------------------------------------
 // Band columns of the type-2 spectrum: per column of B, both output parities
 // of the padded column DFT in one paired transform; rows |qbar| <= Q kept.
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
-k_band_fwd(Members mem, WsOff off, int ldqB, int ncols, int ldq, int Q, AxisTabs<R> ay, int cj) {
+__device__ __forceinline__ void band_fwd_body(int vb, int vg, Members mem, WsOff off, int ldqB, int ncols, int ldq,
+                                              int Q, AxisTabs<R> ay, int cj) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, M = GG::M, G = GG::G, CC = GG::CC, FB = GG::FB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -651,8 +592,8 @@ k_band_fwd(Members mem, WsOff off, int ldqB, int ncols, int ldq, int Q, AxisTabs
   const int items = (ncols + CC - 1) / CC;
   grid_dep_wait();
 #pragma unroll 1
-  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
-    if (it + int(gridDim.x) >= items * mem.count) grid_dep_trigger();  // last item of this CTA
+  for (int it = vb; it < items * mem.count; it += vg) {
+    if (it + vg >= items * mem.count) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     const Member mb = member_at(mem, mi);
     const cpx<R>* __restrict__ B = ws_ptr<cpx<R>>(mb, off.B);
@@ -683,18 +624,25 @@ k_band_fwd(Members mem, WsOff off, int ldqB, int ncols, int ldq, int Q, AxisTabs
   }
 }
 
+template <typename R, int LOG2N>
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
+k_band_fwd(Members mem, WsOff off, int ldqB, int ncols, int ldq, int Q, AxisTabs<R> ay, int cj) {
+  band_fwd_body<R, LOG2N>(blockIdx.x, gridDim.x, mem, off, ldqB, ncols, ldq, Q, ay, cj);
+}
+
 // ---------------------------------------------------------------------------
 // Type-2 interpolation: one warp per polar node.
+// (bx: the block of 8 nodes, mi: the member)
 template <typename R>
-__global__ void __launch_bounds__(256)
-k_interp(Members mem, WsOff off, int ldq, int Q, const int2* __restrict__ q0,
-         const R* __restrict__ wts, const double* __restrict__ D, int n_nodes, int w, int cj) {
+__device__ __forceinline__ void interp_body(int bx, int mi, Members mem, WsOff off, int ldq, int Q,
+                                            const int2* __restrict__ q0, const R* __restrict__ wts,
+                                            const double* __restrict__ D, int n_nodes, int w, int cj) {
   grid_dep_wait();
-  const Member mb = member_at(mem, blockIdx.y);
+  const Member mb = member_at(mem, mi);
   const cpx<R>* __restrict__ Bband = ws_ptr<cpx<R>>(mb, off.Bband);
   cpx<R>* __restrict__ c = ws_ptr<cpx<R>>(mb, off.c);
   const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int j = bx * 8 + (threadIdx.x >> 5);
   if (j >= n_nodes) return;
   const int2 b0 = q0[j];
   const R* wx = wts + size_t(j) * 2 * w;
@@ -726,6 +674,13 @@ k_interp(Members mem, WsOff off, int ldq, int Q, const int2* __restrict__ q0,
   }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_interp(Members mem, WsOff off, int ldq, int Q, const int2* __restrict__ q0,
+         const R* __restrict__ wts, const double* __restrict__ D, int n_nodes, int w, int cj) {
+  interp_body<R>(blockIdx.x, blockIdx.y, mem, off, ldq, Q, q0, wts, D, n_nodes, w, cj);
+}
+
 // ---------------------------------------------------------------------------
 // Type-1 spreading as a gather over TILE x TILE tiles of band cells.  At plan
 // time the (node, stencil origin, ES weights) entries of every node whose
@@ -742,21 +697,21 @@ struct SpreadCfg {
 constexpr int kNumSpreadCfgs = 4;
 constexpr SpreadCfg kSpreadCfgs[kNumSpreadCfgs] = {{8, 4, 128}, {8, 2, 128}, {16, 1, 128}, {16, 2, 64}};
 
+// (item: the work item, mi: the member)
 template <typename R, int TILE, int SPLIT, int CHUNK>
-__global__ void __launch_bounds__(TILE * TILE * SPLIT)
-k_spread(Members mem, WsOff off, const int2* __restrict__ item_range,
-         const int* __restrict__ ent_node, const int2* __restrict__ ent_q0,
-         const R* __restrict__ ent_w, const int* __restrict__ item_tile, int w, int tiles_x, int Q) {
+__device__ __forceinline__ void spread_body(int item, int mi, Members mem, WsOff off,
+                                            const int2* __restrict__ item_range, const int* __restrict__ ent_node,
+                                            const int2* __restrict__ ent_q0, const R* __restrict__ ent_w,
+                                            const int* __restrict__ item_tile, int w, int tiles_x, int Q) {
   constexpr int CELLS = TILE * TILE, THREADS = CELLS * SPLIT;
   __shared__ int2 s_q0[CHUNK];
   __shared__ cpx<R> s_c[CHUNK];
   __shared__ R s_w[CHUNK * 32];
   __shared__ R s_red[2][SPLIT][CELLS];
   grid_dep_wait();
-  const Member mb = member_at(mem, blockIdx.y);
+  const Member mb = member_at(mem, mi);
   const cpx<R>* __restrict__ c = ws_ptr<cpx<R>>(mb, off.c);
   cpx<R>* __restrict__ partial = ws_ptr<cpx<R>>(mb, off.partial);
-  const int item = blockIdx.x;
   const int tile = item_tile[item];
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   const int cell = threadIdx.x & (CELLS - 1), part = threadIdx.x / CELLS;
@@ -798,16 +753,25 @@ k_spread(Members mem, WsOff off, const int2* __restrict__ item_range,
   partial[size_t(item) * CELLS + cell] = mk<R>(ax, ay);
 }
 
+template <typename R, int TILE, int SPLIT, int CHUNK>
+__global__ void __launch_bounds__(TILE * TILE * SPLIT)
+k_spread(Members mem, WsOff off, const int2* __restrict__ item_range,
+         const int* __restrict__ ent_node, const int2* __restrict__ ent_q0,
+         const R* __restrict__ ent_w, const int* __restrict__ item_tile, int w, int tiles_x, int Q) {
+  spread_body<R, TILE, SPLIT, CHUNK>(blockIdx.x, blockIdx.y, mem, off, item_range, ent_node, ent_q0, ent_w,
+                                     item_tile, w, tiles_x, Q);
+}
+
+// (tile: the spreading tile, mi: the member)
 template <typename R, int TILE>
-__global__ void __launch_bounds__(TILE * TILE)
-k_spread_reduce(Members mem, WsOff off, const int* __restrict__ tile_items, int tiles_x,
-                int n_tiles, int Q, int ldq, int cj) {
+__device__ __forceinline__ void spread_reduce_body(int tile, int mi, Members mem, WsOff off,
+                                                   const int* __restrict__ tile_items, int tiles_x, int n_tiles,
+                                                   int Q, int ldq, int cj) {
   constexpr int CELLS = TILE * TILE;
   grid_dep_wait();
-  const Member mb = member_at(mem, blockIdx.y);
+  const Member mb = member_at(mem, mi);
   const cpx<R>* __restrict__ partial = ws_ptr<cpx<R>>(mb, off.partial);
   cpx<R>* __restrict__ Sband = ws_ptr<cpx<R>>(mb, off.Sband);
-  const int tile = blockIdx.x;
   if (tile >= n_tiles) return;
   const int cell = threadIdx.x;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -823,6 +787,13 @@ k_spread_reduce(Members mem, WsOff off, const int* __restrict__ tile_items, int 
     const int e = qx + qy;
     Sband[size_t(qx) * ldq + qy + Q] = mul_ipow(mk<R>(ax, ay), cj ? e : -e);  // (-i)^{q_x+q_y}
   }
+}
+
+template <typename R, int TILE>
+__global__ void __launch_bounds__(TILE * TILE)
+k_spread_reduce(Members mem, WsOff off, const int* __restrict__ tile_items, int tiles_x,
+                int n_tiles, int Q, int ldq, int cj) {
+  spread_reduce_body<R, TILE>(blockIdx.x, blockIdx.y, mem, off, tile_items, tiles_x, n_tiles, Q, ldq, cj);
 }
 
 // Launch the spreading pair with configuration `cfg`: part 0 = k_spread,
@@ -868,8 +839,8 @@ void launch_spread(int cfg, const Members& mem, const WsOff& off, const PlanTabl
 // Inverse band columns: the even and odd rows of each band column of S go
 // through one paired inverse transform; T = even + e^{+2 pi i n/M} odd, n < N.
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
-k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs<R> ay, int cj) {
+__device__ __forceinline__ void band_inv_body(int vb, int vg, Members mem, WsOff off, int ldq, int Q, int ncols,
+                                              int ldqB, AxisTabs<R> ay, int cj) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, M = GG::M, G = GG::G, CC = GG::CC, FB = GG::FB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -883,8 +854,8 @@ k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs
   const int items = (ncols + CC - 1) / CC;
   grid_dep_wait();
 #pragma unroll 1
-  for (int it = blockIdx.x; it < items * mem.count; it += gridDim.x) {
-    if (it + int(gridDim.x) >= items * mem.count) grid_dep_trigger();  // last item of this CTA
+  for (int it = vb; it < items * mem.count; it += vg) {
+    if (it + vg >= items * mem.count) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     const Member mb = member_at(mem, mi);
     const cpx<R>* __restrict__ Sband = ws_ptr<cpx<R>>(mb, off.Sband);
@@ -913,6 +884,12 @@ k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs
   }
 }
 
+template <typename R, int LOG2N>
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COL_MINB))
+k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs<R> ay, int cj) {
+  band_inv_body<R, LOG2N>(blockIdx.x, gridDim.x, mem, off, ldq, Q, ncols, ldqB, ay, cj);
+}
+
 // ---------------------------------------------------------------------------
 // Inverse length-M DFT keeping n < N, split by output parity:
 //   T(2j)   = IDFT_N[W(q) + W(q + N)](j)
@@ -924,9 +901,9 @@ k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs
 // (Mx My) are each formed in FP32 (1/(Mx My) is a power of two, so the
 // scaling is exact), widened exactly, and summed in FP64.
 template <typename R, int LOG2N>
-__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(Geo<R, LOG2N>::MINB_I))
-k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
-          const R* __restrict__ decon_y, R scale, int cj, int bpf, int acc64) {
+__device__ __forceinline__ void row_inv_body(int vb, int vg, Members mem, WsOff off, int ldqA, int ldqB, int Q,
+                                             int ny, AxisTabs<R> ax, const R* __restrict__ decon_y, R scale, int cj,
+                                             int bpf, int acc64) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, RB = GG::RB_I, RS = GG::RS, T = GG::T_RI;
   constexpr bool PF = GG::ROWI_PF;
@@ -965,10 +942,10 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
     cp_async_commit();
   };
   if constexpr (PF)
-    if (int(blockIdx.x) < total) prefetch(blockIdx.x);
+    if (vb < total) prefetch(vb);
 #pragma unroll 1
-  for (int it = blockIdx.x; it < total; it += gridDim.x) {
-    if (it + int(gridDim.x) >= total) grid_dep_trigger();  // last item of this CTA
+  for (int it = vb; it < total; it += vg) {
+    if (it + vg >= total) grid_dep_trigger();  // last item of this CTA
     const int mi = it / items, item = it - mi * items;
     const Member mb = member_at(mem, mi);
     const cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(mb, off.A);
@@ -1023,7 +1000,7 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
         b[m] = cj ? cmul(d, w) : cmulc(d, w);
       }
       __syncthreads();  // every thread has read the landing buffer
-      if (it + int(gridDim.x) < total) prefetch(it + gridDim.x);
+      if (it + vg < total) prefetch(it + vg);
     } else {
       cpx<R> y[16], s[16], sm2[16];
 #pragma unroll
@@ -1090,6 +1067,13 @@ k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
       }
     }
   }
+}
+
+template <typename R, int LOG2N>
+__global__ void __launch_bounds__(Geo<R, LOG2N>::T_RI, min_blocks<R>(Geo<R, LOG2N>::MINB_I))
+k_row_inv(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R> ax,
+          const R* __restrict__ decon_y, R scale, int cj, int bpf, int acc64) {
+  row_inv_body<R, LOG2N>(blockIdx.x, gridDim.x, mem, off, ldqA, ldqB, Q, ny, ax, decon_y, scale, cj, bpf, acc64);
 }
 
 }  // namespace dsnu

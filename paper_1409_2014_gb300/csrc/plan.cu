@@ -398,10 +398,14 @@ static dsnu_status setup_spread(dsnu_plan_s* P, const std::vector<int2>& q0, con
   const dsnu_params& p = P->prm;
   int dev = 0;
   cudaGetDevice(&dev);
+  // The spreading work depends on the node stencils on the fine grid, i.e. on
+  // the polar rule, the disk, the ES width and the fine-grid spacing
+  // pi/(2 l) per axis -- not on the number of grid points -- so plans that
+  // share these share one tuned configuration (a batch of several grid sizes
+  // then has one spreading configuration).
   char key[256];
-  std::snprintf(key, sizeof(key), "%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%d|%d|%d|%d|%d|%d", dev, p.nx, p.ny, p.lx,
-                p.ly, p.cut_radius, p.sigma, p.n_r, p.n_theta, p.kernel_width, p.precision, p.partition,
-                p.radial_rule);
+  std::snprintf(key, sizeof(key), "%d|%.17g|%.17g|%.17g|%d|%d|%d|%d|%d", dev, p.lx, p.ly, p.cut_radius, p.n_r,
+                p.n_theta, p.kernel_width, p.precision, p.radial_rule);
   const char* env = std::getenv("DSNU_AUTOTUNE");
   const bool tune = !(env && env[0] == '0');
   int choice = 0;
