@@ -272,3 +272,48 @@ def test_sharp_partition_with_a_decayed_tail_reduces_to_the_polar_quadrature():
     assert np.abs(i1).max() / scale < 5e-11
     assert np.abs(i2 - ex).max() / scale < 5e-11
     assert rel_linf(phi, ex) < 1e-12
+
+
+def _naive_dft2(x, sign):
+    """Literal 2D DFT: X[k, l] = sum_m sum_n x[m, n] e^{sign 2 pi i (k m / M_y + l n / M_x)}."""
+    my, mx = x.shape
+    out = np.zeros((my, mx), dtype=np.complex128)
+    for k in range(my):
+        for l in range(mx):
+            acc = 0j
+            for m in range(my):
+                for n in range(mx):
+                    acc += x[m, n] * complex(math.cos(sign * 2 * math.pi * (k * m / my + l * n / mx)),
+                                             math.sin(sign * 2 * math.pi * (k * m / my + l * n / mx)))
+            out[k, l] = acc
+    return out
+
+
+@pytest.mark.parametrize("nx,ny", [(16, 16), (16, 8)])
+def test_i1_against_a_literal_dft_on_small_grids(nx, ny):
+    """I1 (eq. SubInt1) with its padded FFT replaced by the literal double sum of
+    the DFT definition (kappa = 2: a 32 x 32 or 16 x 32 sum), written here
+    without the oracle's FFT library or frequency helpers: the angular
+    frequency of index q on M points of spacing h is 2 pi qbar / (M h), qbar
+    the signed index."""
+    lx, ly, P = 4.0, 2.0 * ny / nx * 2.0, 2.5
+    rho = synth.density_sum(nx, ny, lx, ly, seed=21, count=3)
+    p = OracleParams(nx=nx, ny=ny, lx=lx, ly=ly, cut_radius=P, n_r=8, n_theta=16)
+    my, mx = 2 * ny, 2 * nx
+    pad = np.zeros((my, mx))
+    pad[:ny, :nx] = rho
+    R = _naive_dft2(pad, -1.0)
+    hx, hy = 2 * lx / nx, 2 * ly / ny
+    sig2 = (P / 6.0) ** 2
+    for k in range(my):
+        for l in range(mx):
+            kb = k if k < my // 2 else k - my
+            lb = l if l < mx // 2 else l - mx
+            wy, wx = 2 * math.pi * kb / (my * hy), 2 * math.pi * lb / (mx * hx)
+            s = wx * wx + wy * wy
+            R[k, l] *= 0.0 if s == 0 else -(wx * wx / s) * (1.0 - math.exp(-s / sig2))
+    back = _naive_dft2(R, +1.0) / (mx * my)
+    want = back[:ny, :nx].real
+    got = O.i1_padded_fft(rho, p)
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+    assert np.abs(back[:ny, :nx].imag).max() <= 1e-13 * np.abs(want).max()
