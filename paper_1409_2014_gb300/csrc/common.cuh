@@ -507,6 +507,48 @@ __device__ __forceinline__ double to_f64(R v) {
   return static_cast<double>(v);
 }
 
+// double(a) + double(b) rounded to FP64 (round to nearest even), bit for bit,
+// for FP32 a and b, without FP64 instructions on the common path (this GPU
+// runs FP64 at 1/63 of its FP32 rate):
+//  * TwoSum (Knuth): s = fl32(a + b) and the exact remainder e, s + e = a + b,
+//    |e| <= half an FP32 ulp of s;
+//  * double(s) has 29 zero low fraction bits, so the FP64 sum is the FP64 bit
+//    pattern of s plus e counted in FP64 ulps of s, rounded to the nearest
+//    integer, ties to even (the pattern's last bit being 0); s + e stays in
+//    the binade of s, except below a power of two s when e has the other
+//    sign, where the count is in the lower binade's ulps (half as large) and
+//    the pattern steps down into that binade;
+//  * the count is e scaled by a power of two (exact) and converted with
+//    round-to-nearest-even; it is at most 2^29 in magnitude.
+// s with a biased exponent below 53 (|s| < 2^-74, where the scale would leave
+// the float range), infinite or NaN takes the FP64 addition, in a branch that
+// a warp enters only when one of its lanes needs it, through an out-of-line
+// function: the compiler would otherwise turn the branch into predicated
+// instructions, and a predicated-off FP64 instruction still occupies the
+// narrow FP64 pipe.
+static __device__ __noinline__ double add_f64_of_f32(float a, float b) {
+  return static_cast<double>(a) + static_cast<double>(b);
+}
+
+__device__ __forceinline__ double add_f32_f64(float a, float b) {
+  const float s = a + b;
+  const float bv = s - a;
+  const float av = s - bv;
+  const float e = (a - av) + (b - bv);
+  const unsigned u = __float_as_uint(s), v = __float_as_uint(e);
+  const unsigned es = (u >> 23) & 0xFFu;
+  const bool down = ((u & 0x7FFFFFu) == 0u) && ((u ^ v) & 0x80000000u) && (e != 0.0f);
+  const float scale = __uint_as_float((306u - es + (down ? 1u : 0u)) << 23);  // 2^(52 - E) or 2^(53 - E)
+  const int r = __float2int_rn(e * scale);
+  const long long d = (u & 0x80000000u) ? -(long long)r : (long long)r;  // along the magnitude of s
+  const unsigned hi = (u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + 0x38000000u);
+  double out = __longlong_as_double((long long)(((unsigned long long)hi << 32) | (u << 29)) + d);
+  const bool slow = es < 53u || es == 255u;
+  if (__any_sync(__activemask(), slow))
+    if (slow) out = add_f64_of_f32(a, b);
+  return out;
+}
+
 // expm1 in the working precision (library function).
 template <typename R>
 __device__ __forceinline__ R expm1_r(R x) {

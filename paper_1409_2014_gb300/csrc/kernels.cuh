@@ -899,7 +899,8 @@ k_band_inv(Members mem, WsOff off, int ldq, int Q, int ncols, int ldqB, AxisTabs
 // Phi must be 16-byte aligned (checked on the host).  With acc64 (FP32 plans)
 // Phi = I1 + I2 is added in FP64: I1 = Re T / (Mx My) and I2 = Im T dx dy /
 // (Mx My) are each formed in FP32 (1/(Mx My) is a power of two, so the
-// scaling is exact), widened exactly, and summed in FP64.
+// scaling is exact), and their FP64 sum is formed by add_f32_f64 (bitwise
+// the FP64 addition of the two widened terms).
 template <typename R, int LOG2N>
 __device__ __forceinline__ void row_inv_body(int vb, int vg, Members mem, WsOff off, int ldqA, int ldqB, int Q,
                                              int ny, AxisTabs<R> ax, const R* __restrict__ decon_y, R scale, int cj,
@@ -1049,8 +1050,8 @@ __device__ __forceinline__ void row_inv_body(int vb, int vg, Members mem, WsOff 
           const R ia = cj ? -a[m].y : a[m].y;
           const R ib = cj ? -b[m].y : b[m].y;
           double2 out;
-          out.x = to_f64<R>(a[m].x * scale) + to_f64<R>(ia * ax.decon[n] * dys);
-          out.y = to_f64<R>(b[m].x * scale) + to_f64<R>(ib * ax.decon[n + 1] * dys);
+          out.x = add_f32_f64(float(a[m].x * scale), float(ia * ax.decon[n] * dys));
+          out.y = add_f32_f64(float(b[m].x * scale), float(ib * ax.decon[n + 1] * dys));
           *reinterpret_cast<double2*>(phi + size_t(row) * N + n) = out;
         }
       } else {
