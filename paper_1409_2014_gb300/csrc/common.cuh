@@ -471,11 +471,12 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 // while data lands in its shared memory, and the caller returns without
 // writing results.  Returns true when the CTA must stop; it is a barrier for
 // the whole CTA either way.
-__device__ __forceinline__ bool cta_timed_out(bool ok, unsigned long long* bar, unsigned parity, int* status) {
+__device__ __forceinline__ bool cta_timed_out(bool ok, unsigned long long* bar, unsigned parity, int* status,
+                                              unsigned long long drain_ns = 1000000000ull) {
   if (!__syncthreads_or(!ok)) return false;
   if (threadIdx.x == 0) {
     atomicExch(status, int(DSNU_ETIMEOUT));
-    mbar_wait(bar, parity, 1000000000ull);
+    mbar_wait(bar, parity, drain_ns);
   }
   return true;
 }

@@ -1,8 +1,9 @@
 """The bounded mbarrier wait and the asynchronous copies the prefetching row
 passes use (common.cuh): an expired wait returns false after its limit (the
 status path, exercised with a phase that nothing completes; no fault, no
-hang), an arrival and a bulk copy complete their phases, and bulk and
-cp.async copies deliver their data."""
+hang), an arrival and a bulk copy complete their phases, bulk and cp.async
+copies deliver their data, and a CTA whose wait expired records
+DSNU_ETIMEOUT and returns without writing (cta_timed_out)."""
 
 import os
 import shutil
