@@ -918,11 +918,21 @@ __device__ __forceinline__ void row_inv_body(int vb, int vg, Members mem, WsOff 
   else copy_to_smem(stw, ax.stw, GG::STW);
   if constexpr (GG::ROW_TAB)
     for (int i = threadIdx.x; i < (PF ? N / 2 : N); i += T) wtab[i] = twm(ax, i);
-  __syncthreads();
-  grid_dep_wait();
   const int tid = threadIdx.x;
   const int rr = GG::ILV_I ? (tid & 1) : tid / G;
   const int t = GG::ILV_I ? (tid >> 1) : tid - rr * G;
+  // FP32: the deconvolution factors of the outputs n = 2 (t + G m) + {0, 1}
+  // this thread writes, the same for every row: kept in registers for the
+  // whole launch (loaded per item, at the end of each transform, they came
+  // from L2 and stalled the stores)
+  constexpr int ND = sizeof(R) == 4 ? 8 : 1;
+  float2 dec[ND];
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) dec[m] = *reinterpret_cast<const float2*>(ax.decon + 2 * (t + G * m));
+  }
+  __syncthreads();
+  grid_dep_wait();
   const int si = cj ? -1 : 1;
   cpx<R>* buf_u = sm + (2 * rr) * RS;
   cpx<R>* buf_v = buf_u + RS;
@@ -1050,8 +1060,8 @@ __device__ __forceinline__ void row_inv_body(int vb, int vg, Members mem, WsOff 
           const R ia = cj ? -a[m].y : a[m].y;
           const R ib = cj ? -b[m].y : b[m].y;
           double2 out;
-          out.x = add_f32_f64(float(a[m].x * scale), float(ia * ax.decon[n] * dys));
-          out.y = add_f32_f64(float(b[m].x * scale), float(ib * ax.decon[n + 1] * dys));
+          out.x = add_f32_f64(float(a[m].x * scale), float(ia * R(dec[m].x) * dys));
+          out.y = add_f32_f64(float(b[m].x * scale), float(ib * R(dec[m].y) * dys));
           *reinterpret_cast<double2*>(phi + size_t(row) * N + n) = out;
         }
       } else {
@@ -1061,8 +1071,10 @@ __device__ __forceinline__ void row_inv_body(int vb, int vg, Members mem, WsOff 
           const R ia = cj ? -a[m].y : a[m].y;
           const R ib = cj ? -b[m].y : b[m].y;
           double2 out;
-          out.x = to_f64<R>((a[m].x + ia * ax.decon[n] * dy) * scale);
-          out.y = to_f64<R>((b[m].x + ib * ax.decon[n + 1] * dy) * scale);
+          const R d0 = (sizeof(R) == 4) ? R(dec[m & (ND - 1)].x) : ax.decon[n];
+          const R d1 = (sizeof(R) == 4) ? R(dec[m & (ND - 1)].y) : ax.decon[n + 1];
+          out.x = to_f64<R>((a[m].x + ia * d0 * dy) * scale);
+          out.y = to_f64<R>((b[m].x + ib * d1 * dy) * scale);
           *reinterpret_cast<double2*>(phi + size_t(row) * N + n) = out;
         }
       }
