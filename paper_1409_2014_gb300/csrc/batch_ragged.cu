@@ -107,7 +107,7 @@ __device__ __forceinline__ int rag_group(const RagTable& T, int s, int b) {
 #define DSNU_RAG_ROWF(L) \
   row_fwd_body<float, L>(vb, vg, a.mem, a.off, a.ldqA, a.ldqB, a.Q, a.ny, a.ax, a.decon_y, 0, a.status)
 #define DSNU_RAG_BANDF(L) band_fwd_body<float, L>(vb, vg, a.mem, a.off, a.ldqB, a.Q + 1, a.ldq, a.Q, a.ay, 0)
-#define DSNU_RAG_COL(L) col_main_body<float, L, false>(vb, vg, a.mem, a.off, a.ldqA, a.nx + 1, a.ay, a.mt, 0)
+#define DSNU_RAG_COL(L) col_main_body<float, L, false>(vb, vg, a.mem, a.off, a.ldqA, a.nx + 1, a.ay, a.mt, 0, nullptr)
 #define DSNU_RAG_BANDI(L) band_inv_body<float, L>(vb, vg, a.mem, a.off, a.ldq, a.Q, a.Q + 1, a.ldqB, a.ay, 0)
 #define DSNU_RAG_ROWI(L)                                                                                       \
   row_inv_body<float, L>(vb, vg, a.mem, a.off, a.ldqA, a.ldqB, a.Q, a.ny, a.ax, a.decon_y, a.scale, 0, a.bpf, \
@@ -291,7 +291,7 @@ dsnu_status ragged_create(const RaggedGroupIn* groups, int n, Ragged** out) {
     a.mem.dev = groups[i].dev_members;
     a.mem.one = groups[i].first;
     a.mem.count = groups[i].count;
-    a.off = WsOff{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial};
+    a.off = WsOff{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial, L.off_sched};
     a.ax = AxisTabs<float>{static_cast<const cpx<float>*>(t.stw_x), static_cast<const cpx<float>*>(t.twm_lo_x),
                            static_cast<const cpx<float>*>(t.twm_hi_x), g.log2lo_x,
                            static_cast<const float*>(t.decon_x), static_cast<const cpx<float>*>(t.stwc_x)};
@@ -436,7 +436,7 @@ dsnu_status ragged_enqueue(const Ragged* R, cudaStream_t st) {
       m.dev = gi.dev_members;
       m.one = gi.first;
       m.count = gi.count;
-      const WsOff off{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial};
+      const WsOff off{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial, L.off_sched};
       launch_spread<float>(p->geom.spread_cfg, m, off, p->tab, p->geom, L.ldq, 0, bs, 2, pdl);
     }
   }

@@ -30,6 +30,9 @@ struct PlanTables {
   void* m_gy;     // real, n_gy    1 - exp(-(a dk_y)^2/sigma^2), a < n_gy
   void* m_kx;     // real, k_x per column for the sin 2theta term (0 at the Nyquist column); generic only
   int2* node_q0;  // n_nodes
+  int* itile_ptr;   // n_itiles + 1: interpolation item -> range of itile_nodes
+  int2* itile_org;  // n_itiles: the item's tile's first (q_x, q_y) (its nodes' stencil origins from there)
+  int* itile_nodes; // n_nodes: node indices grouped by the tile of their stencil origin
   void* node_w;   // real, n_nodes * 2w (x weights then y weights)
   double* node_D; // n_nodes
   int* tile_items;  // n_tiles + 1: spreading tile -> range of work items
@@ -62,7 +65,8 @@ struct Members {
 
 // Workspace layout (offsets in bytes from the workspace base).
 struct WsLayout {
-  size_t off_A, off_B, off_Bband, off_Sband, off_c, off_partial, total;
+  // off_sched: the column pass's work counter (one int, reset by the forward row pass)
+  size_t off_A, off_B, off_Bband, off_Sband, off_c, off_partial, off_sched, total;
   int ldqA, ldqB, ldq;  // q columns of the row-tiled A and B; band column length
 };
 
@@ -76,6 +80,7 @@ struct PlanGeom {
   int row_pf;              // bit 0 forward row prefetch, bit 1 inverse, bit 2 rowi_bpf
   size_t smem_rowi;        // its dynamic shared memory per CTA
   int w, Q, n_nodes, n_tiles, tiles_x, tiles_y, max_tile_nodes, n_items;
+  int n_itiles;            // interpolation items (at most kItileNodes nodes of one kItile x kItile tile)
   int spread_cfg;          // index into kSpreadCfgs (chosen by the autotuner)
   int spread_tile;         // its tile edge (cells)
   int precision, sharp;

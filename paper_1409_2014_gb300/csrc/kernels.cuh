@@ -13,9 +13,11 @@
 //               times m1 = (1 - p) (-k_x^2/|k|^2) (eq. SubInt1), inverse
 //               column DFT keeping N rows; in place.               [I1]
 //   k_band_fwd: per column q_x in [0, Q] of B: column DFT, keep |q_y| <= Q.
-//   k_interp  : rho_hat(k_j) = sum over the w x w ES stencil of the band
+//   k_interp_tile: rho_hat(k_j) = sum over the w x w ES stencil of the band
 //               (type-2 NUFFT, eq. 2.2); c_j = D_j rho_hat_j with the polar
-//               weights of eq. I2PolarDisc (FP64 multiply).
+//               weights of eq. I2PolarDisc (FP64 multiply); per tile of
+//               stencil origins, the band values it reaches staged in shared
+//               memory.
 //   k_spread  : S(q) = sum_j c_j phi(u_j - q) on the band (type-1 NUFFT
 //               spreading, eq. 2.1), gathered per tile from a node list
 //               (no atomics).
@@ -172,7 +174,7 @@ __device__ __forceinline__ R mult_high(const MultTabs<R>& mt, R wx2, R kx, R gx,
 
 // Workspace offsets (bytes) of one member's buffers, and member access.
 struct WsOff {
-  size_t A, B, Bband, Sband, c, partial;
+  size_t A, B, Bband, Sband, c, partial, sched;
 };
 __device__ __forceinline__ Member member_at(const Members& m, int i) { return m.count == 1 ? m.one : m.dev[i]; }
 template <typename T>
@@ -302,6 +304,8 @@ __device__ __forceinline__ void row_fwd_body(int vb, int vg, Members mem, WsOff 
     if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
   grid_dep_wait();
+  // the column pass that follows hands out its columns from this counter
+  if (vb == 0 && threadIdx.x == 0 && mem.count > 0) *ws_ptr<int>(member_at(mem, 0), off.sched) = 0;
   const int tid = threadIdx.x;
   const int rr = GG::ILV_F ? (tid & 1) : tid / G;
   const int t = GG::ILV_F ? (tid >> 1) : tid - rr * G;
@@ -429,7 +433,7 @@ k_row_fwd(Members mem, WsOff off, int ldqA, int ldqB, int Q, int ny, AxisTabs<R>
 // precede the first barrier, so the in-place update is safe.
 template <typename R, int LOG2N, bool GEN>
 __device__ __forceinline__ void col_main_body(int vb, int vg, Members mem, WsOff off, int ldqA, int ncols,
-                                              AxisTabs<R> ay, MultTabs<R> mt, int cj) {
+                                              AxisTabs<R> ay, MultTabs<R> mt, int cj, int* ctr) {
   using GG = Geo<R, LOG2N>;
   constexpr int N = GG::N, G = GG::G, CC = GG::CC, FB = GG::FB;
   // FP32 with the DS multiplier: the e^{-2 pi i n/M} factors of the odd chain
@@ -483,12 +487,28 @@ __device__ __forceinline__ void col_main_body(int vb, int vg, Members mem, WsOff
     for (int m = 0; m < (PF ? 16 : 1); ++m)
       x[m] = (col2 < ncols) ? A2[Tile<R>::at(t + G * m, col2, ldqA)] : mk<R>(R(0), R(0));
   };
+  // Items: CTA vb starts with item vb; with a work counter (`ctr`, zeroed by
+  // the row pass before) each CTA then takes the next free item, item vg + c
+  // for the counter's value c, else items vb + vg, vb + 2 vg, ...  Taken from
+  // a counter, a CTA that runs slower than the others (persistent CTAs that a
+  // programmatic launch placed as the previous kernel's CTAs drained ran up to
+  // 15 % slower, leaving the last ones 40 us behind) takes fewer columns.
+  // s_next[(kk + 1) & 1] carries the item after `nxt` from thread 0 to the
+  // others across the transforms' barriers.
+  __shared__ int s_next[2];
+  int nxt = vb + vg;  // the item after `it`
+  if (ctr) {
+    if (tid == 0) s_next[0] = (vb < total) ? vg + atomicAdd(ctr, 1) : total;
+    __syncthreads();
+    nxt = s_next[0];
+  }
   if constexpr (PF)
     if (vb < total) load_col(vb, xn);
   int kk = 0;  // items done by this CTA (the multiplier buffer is kk & 1)
 #pragma unroll 1
-  for (int it = vb; it < total; it += vg, ++kk) {
-    if (it + vg >= total) grid_dep_trigger();  // last item of this CTA
+  for (int it = vb; it < total; ++kk) {
+    if (nxt >= total) grid_dep_trigger();  // last item of this CTA
+    if (ctr && tid == 0) s_next[(kk + 1) & 1] = (nxt < total) ? vg + atomicAdd(ctr, 1) : total;
     const int mi = it / items, item = it - mi * items;
     cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(member_at(mem, mi), off.A);
     const int col = item * CC + cl;
@@ -546,11 +566,11 @@ __device__ __forceinline__ void col_main_body(int vb, int vg, Members mem, WsOff
       }
     }
     if constexpr (PF)
-      if (it + vg < total) load_col(it + vg, xn);
+      if (nxt < total) load_col(nxt, xn);
     // the next item's m1 rows into the other buffer (last read by the item
     // before this one, whose reads the barriers since then have completed)
     if constexpr (TAB)
-      if (it + vg < total) fetch_mult(it + vg, (kk + 1) & 1);
+      if (nxt < total) fetch_mult(nxt, (kk + 1) & 1);
     block_fft2_regs<R, LOG2N>(e, o, buf_e, buf_o, t, stw, cj == 0);
     if (valid) {
 #pragma unroll
@@ -562,13 +582,16 @@ __device__ __forceinline__ void col_main_body(int vb, int vg, Members mem, WsOff
         A[Tile<R>::at(n, col, ldqA)] = cj ? e[m] + cmul(o[m], w) : e[m] + cmulc(o[m], w);
       }
     }
+    it = nxt;
+    nxt = ctr ? s_next[(kk + 1) & 1] : nxt + vg;
   }
 }
 
 template <typename R, int LOG2N, bool GEN>
 __global__ void __launch_bounds__(Geo<R, LOG2N>::T_C, min_blocks<R>(DSNU_COLMAIN_MINB))
 k_col_main(Members mem, WsOff off, int ldqA, int ncols, AxisTabs<R> ay, MultTabs<R> mt, int cj) {
-  col_main_body<R, LOG2N, GEN>(blockIdx.x, gridDim.x, mem, off, ldqA, ncols, ay, mt, cj);
+  col_main_body<R, LOG2N, GEN>(blockIdx.x, gridDim.x, mem, off, ldqA, ncols, ay, mt, cj,
+                               ws_ptr<int>(member_at(mem, 0), off.sched));
 }
 
 
@@ -631,7 +654,8 @@ k_band_fwd(Members mem, WsOff off, int ldqB, int ncols, int ldq, int Q, AxisTabs
 }
 
 // ---------------------------------------------------------------------------
-// Type-2 interpolation: one warp per polar node.
+// Type-2 interpolation: one warp per polar node, gathering from the band
+// array (the stage launches of ragged batches).
 // (bx: the block of 8 nodes, mi: the member)
 template <typename R>
 __device__ __forceinline__ void interp_body(int bx, int mi, Members mem, WsOff off, int ldq, int Q,
@@ -674,12 +698,92 @@ __device__ __forceinline__ void interp_body(int bx, int mi, Members mem, WsOff o
   }
 }
 
+// The interpolation of single plans, by tiles of stencil origins (interp_body,
+// one warp per node gathering straight from the band array, serves the
+// stage launches of ragged batches): the plan groups the
+// nodes by the kItile x kItile tile of the (q_x, q_y) plane that holds their
+// stencil origin, in work items of at most kItileNodes nodes of one tile; one
+// CTA per item copies the (kItile + w - 1)^2 band values
+// its stencils reach into shared memory (whole band columns' runs, read
+// coalesced once; the Hermitian fold for q_x < 0 and the centring phase
+// applied on the way; zero outside the band) and then runs every node's
+// stencil sum from there, four threads per node (the same terms as
+// interp_body, summed in another order).  The band values are read once per
+// item instead of once per stencil that covers them, in runs rather than in
+// scattered 8-byte loads, and a CTA starts all its nodes at once, which is what
+// makes the stage fast on the few SMs it gets next to the column pass.
+constexpr int kItile = 32;       // tile edge (stencil origins)
+constexpr int kItileNodes = 64;  // nodes per work item at most (four threads each: 256)
+template <typename R>
+__device__ __forceinline__ void interp_tile_body(int tile, int mi, Members mem, WsOff off, int ldq, int Q,
+                                                 const int2* __restrict__ q0, const R* __restrict__ wts,
+                                                 const double* __restrict__ D, const int* __restrict__ tile_ptr,
+                                                 const int2* __restrict__ tile_org,
+                                                 const int* __restrict__ tile_nodes, int w, int cj) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* reg = reinterpret_cast<cpx<R>*>(smem_raw);  // [dx][dy], S x S
+  const int S = kItile + w - 1;
+  const int2 org = tile_org[tile];
+  const int n0 = tile_ptr[tile], n1 = tile_ptr[tile + 1];
+  // four threads per node (an item holds at most 64), thread h of a node
+  // taking the stencil rows b = h, h + 4, ...; the node's plan data are
+  // fetched before the wait for the band values
+  const int s = threadIdx.x >> 2, h = threadIdx.x & 3;
+  const bool have = n0 + s < n1;
+  const int j = have ? tile_nodes[n0 + s] : 0;
+  const int2 b0 = have ? q0[j] : make_int2(0, 0);
+  const double d = have ? D[j] : 0.0;
+  grid_dep_wait();
+  const Member mb = member_at(mem, mi);
+  const cpx<R>* __restrict__ Bband = ws_ptr<cpx<R>>(mb, off.Bband);
+  cpx<R>* __restrict__ c = ws_ptr<cpx<R>>(mb, off.c);
+  for (int i = threadIdx.x; i < S * S; i += blockDim.x) {
+    const int dx = i / S, dy = i - dx * S;
+    const int qx = org.x + dx, qy = org.y + dy;
+    cpx<R> v = mk<R>(R(0), R(0));
+    if (qx <= Q && qx >= -Q && qy <= Q && qy >= -Q) {
+      if (qx >= 0) {
+        v = Bband[size_t(qx) * ldq + qy + Q];
+      } else {
+        v = conj(Bband[size_t(-qx) * ldq + (Q - qy)]);
+      }
+      const int e = qx + qy;
+      v = mul_ipow(v, cj ? -e : e);  // centring phase i^{q_x + q_y}
+    }
+    reg[i] = v;
+  }
+  __syncthreads();
+  R ax = R(0), ay = R(0);
+  if (have) {
+    const R* wx = wts + size_t(j) * 2 * w;
+    const R* wy = wx + w;
+    const cpx<R>* rb = reg + (b0.x - org.x) * S + (b0.y - org.y);
+    for (int b = h; b < w; b += 4) {
+      const R fy = wy[b];
+      for (int a = 0; a < w; ++a) {
+        const cpx<R> v = rb[a * S + b];
+        const R f = wx[a] * fy;
+        ax += f * v.x;
+        ay += f * v.y;
+      }
+    }
+  }
+  ax += __shfl_xor_sync(0xffffffffu, ax, 1);
+  ay += __shfl_xor_sync(0xffffffffu, ay, 1);
+  ax += __shfl_xor_sync(0xffffffffu, ax, 2);
+  ay += __shfl_xor_sync(0xffffffffu, ay, 2);
+  // the four partial sums of a node (lanes 4 s' .. 4 s' + 3 of the warp)
+  if (have && h == 0) c[j] = mk<R>(R(d * double(ax)), R(d * double(ay)));
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256)
-k_interp(Members mem, WsOff off, int ldq, int Q, const int2* __restrict__ q0,
-         const R* __restrict__ wts, const double* __restrict__ D, int n_nodes, int w, int cj) {
-  interp_body<R>(blockIdx.x, blockIdx.y, mem, off, ldq, Q, q0, wts, D, n_nodes, w, cj);
+k_interp_tile(Members mem, WsOff off, int ldq, int Q, const int2* __restrict__ q0, const R* __restrict__ wts,
+              const double* __restrict__ D, const int* __restrict__ tile_ptr, const int2* __restrict__ tile_org,
+              const int* __restrict__ tile_nodes, int w, int cj) {
+  interp_tile_body<R>(blockIdx.x, blockIdx.y, mem, off, ldq, Q, q0, wts, D, tile_ptr, tile_org, tile_nodes, w, cj);
 }
+inline size_t interp_tile_smem(int w, size_t csz) { return size_t(kItile + w - 1) * size_t(kItile + w - 1) * csz; }
 
 // ---------------------------------------------------------------------------
 // Type-1 spreading as a gather over TILE x TILE tiles of band cells.  At plan

@@ -205,7 +205,7 @@ template <typename R>
 dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout& L, const Members& mem,
                          cudaStream_t st, int cj, cudaEvent_t* ev, const Overlap* ov) {
   if (g.standard) return run_standard<R>(g, t, L, mem, st, cj, ev);
-  const WsOff off{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial};
+  const WsOff off{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial, L.off_sched};
   const AxisTabs<R> ax{static_cast<const cpx<R>*>(t.stw_x), static_cast<const cpx<R>*>(t.twm_lo_x),
                        static_cast<const cpx<R>*>(t.twm_hi_x), g.log2lo_x, static_cast<const R*>(t.decon_x),
                        static_cast<const cpx<R>*>(t.stwc_x)};
@@ -262,8 +262,9 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
       default: return DSNU_EUNSUPPORTED;
     }
     if (marks) DSNU_MARK(2);
-    launch_k(g.pdl != 0, k_interp<R>, dim3((g.n_nodes + 7) / 8, mem.count), dim3(256), 0, bst, mem, off, L.ldq,
-             g.Q, t.node_q0, wts, t.node_D, g.n_nodes, g.w, cj);
+    launch_k(g.pdl != 0, k_interp_tile<R>, dim3(g.n_itiles, mem.count), dim3(256),
+             interp_tile_smem(g.w, sizeof(cpx<R>)), bst, mem, off, L.ldq, g.Q, t.node_q0, wts, t.node_D, t.itile_ptr,
+             t.itile_org, t.itile_nodes, g.w, cj);
     if (marks) DSNU_MARK(3);
     launch_spread<R>(g.spread_cfg, mem, off, t, g, L.ldq, cj, bst, 0, g.pdl != 0);
     if (marks) DSNU_MARK(4);
@@ -328,7 +329,7 @@ dsnu_status run_pipeline(const PlanGeom& g, const PlanTables& t, const WsLayout&
 
 template <typename R>
 cudaError_t time_spread(const PlanGeom& g, const PlanTables& t, const WsLayout& L, void* ws, int reps, float* ms) {
-  const WsOff off{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial};
+  const WsOff off{L.off_A, L.off_B, L.off_Bband, L.off_Sband, L.off_c, L.off_partial, L.off_sched};
   const Members mem = single_member(nullptr, nullptr, ws);
   cudaEvent_t e0, e1;
   cudaError_t e = cudaEventCreate(&e0);

@@ -199,6 +199,8 @@ struct HostTables {
   std::vector<R> stw_x, stwc_x, twm_lo_x, twm_hi_x, decon_x, stw_y, twm_lo_y, twm_hi_y, decon_y;
   std::vector<R> m_wx2, m_gx, m_gy, m_kx;
   std::vector<int2> node_q0;
+  std::vector<int> itile_ptr, itile_nodes;
+  std::vector<int2> itile_org;
   std::vector<R> node_w;
   std::vector<double> node_D;
 };
@@ -601,6 +603,36 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
     return fail(DSNU_EINVAL, "disk plus ES stencil does not fit the padded grid: need P*h + w*pi/M < pi");
   g.Q = Q;
 
+  // interpolation items: nodes grouped by the kItile x kItile tile of the
+  // plane of stencil origins q0 in [-Q, Q]^2 that holds theirs (node order
+  // kept within a tile), each tile's nodes cut into items of at most
+  // kItileNodes (the polar nodes crowd near the origin: a whole ring of small
+  // radius falls in one tile); only tiles with nodes are listed
+  {
+    const int nt = (2 * Q + 1 + kItile - 1) / kItile;
+    std::vector<int> cnt(size_t(nt) * nt, 0);
+    std::vector<int> tix(nn);
+    for (int j = 0; j < nn; ++j) {
+      const int tx = (T.node_q0[j].x + Q) / kItile, ty = (T.node_q0[j].y + Q) / kItile;
+      tix[j] = tx * nt + ty;
+      ++cnt[tix[j]];
+    }
+    std::vector<int> first(size_t(nt) * nt, -1);
+    T.itile_ptr.assign(1, 0);
+    T.itile_org.clear();
+    for (int t = 0; t < nt * nt; ++t)
+      if (cnt[t] > 0) {
+        first[t] = T.itile_ptr.back();
+        for (int k = 0; k < cnt[t]; k += kItileNodes) {
+          T.itile_ptr.push_back(T.itile_ptr.back() + std::min(kItileNodes, cnt[t] - k));
+          T.itile_org.push_back(make_int2(-Q + (t / nt) * kItile, -Q + (t % nt) * kItile));
+        }
+      }
+    T.itile_nodes.assign(nn, 0);
+    for (int j = 0; j < nn; ++j) T.itile_nodes[first[tix[j]]++] = j;
+    g.n_itiles = int(T.itile_org.size());
+  }
+
   // one device block for every table
   Builder b;
   const size_t o_stx = b.add(T.stw_x), o_tlx = b.add(T.twm_lo_x), o_thx = b.add(T.twm_hi_x);
@@ -609,6 +641,7 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   const size_t o_dy = b.add(T.decon_y);
   const size_t o_wx2 = b.add(T.m_wx2), o_gx = b.add(T.m_gx), o_gy = b.add(T.m_gy), o_kx = b.add(T.m_kx);
   const size_t o_q0 = b.add(T.node_q0), o_w = b.add(T.node_w), o_D = b.add(T.node_D);
+  const size_t o_itp = b.add(T.itile_ptr), o_ito = b.add(T.itile_org), o_itn = b.add(T.itile_nodes);
   const int zero = 0;
   const size_t o_st = b.add(&zero, sizeof(int));
   void* dev = nullptr;
@@ -627,6 +660,9 @@ static dsnu_status build_tables(dsnu_plan_s* P, cudaStream_t st) {
   t.stw_y = d + o_sty; t.twm_lo_y = d + o_tly; t.twm_hi_y = d + o_thy; t.decon_y = d + o_dy;
   t.m_wx2 = d + o_wx2; t.m_gx = d + o_gx; t.m_gy = d + o_gy; t.m_kx = d + o_kx;
   t.node_q0 = reinterpret_cast<int2*>(d + o_q0);
+  t.itile_ptr = reinterpret_cast<int*>(d + o_itp);
+  t.itile_org = reinterpret_cast<int2*>(d + o_ito);
+  t.itile_nodes = reinterpret_cast<int*>(d + o_itn);
   t.node_w = d + o_w;
   t.node_D = reinterpret_cast<double*>(d + o_D);
   t.status = reinterpret_cast<int*>(d + o_st);
@@ -711,6 +747,7 @@ static void layout_workspace(dsnu_plan_s* P) {  // defined after the autotuner, 
   L.off_Sband = take(size_t(g.Q + 1) * L.ldq * csz);
   L.off_c = take(size_t(g.n_nodes) * csz);
   L.off_partial = take(size_t(std::max(g.n_items, 1)) * g.spread_tile * g.spread_tile * csz);
+  L.off_sched = take(sizeof(int));
   L.total = off;
 }
 
@@ -824,14 +861,16 @@ dsnu_status dsnu_plan_create_multiplier(const dsnu_params* params, const dsnu_mu
   }
   layout_workspace(P);
   // mixed plans on large grids: the band chain runs next to the column pass
-  // on a low-priority side stream, the column pass leaving 12 of every 152 SMs
-  // free (measured best at 4096^2 on GB300: 0.613 -> 0.586 ms per solve);
+  // on a low-priority side stream, the column pass leaving 16 of every 152 SMs
+  // free (measured best at 4096^2 on GB300 over 0..24 SMs, with the column
+  // pass's work counter and the tiled interpolation: 0.5137 ms against
+  // 0.5226 with 12 and 0.534 with the band chain in line);
   // DSNU_BAND_SMS=<n> sets the number of SMs, 0 turns it off
   if (p.precision == DSNU_MIXED && !standard) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int reserve = (p.nx >= 2048 && p.ny >= 2048) ? std::max(1, (sms * 12 + 76) / 152) : 0;
+    int reserve = (p.nx >= 2048 && p.ny >= 2048) ? std::max(1, (sms * 16 + 76) / 152) : 0;
     const char* env = std::getenv("DSNU_BAND_SMS");
     if (env) reserve = std::atoi(env);
     if (reserve > 0) {
