@@ -494,7 +494,7 @@ __device__ __forceinline__ void col_main_body(int vb, int vg, Members mem, WsOff
   // programmatic launch placed as the previous kernel's CTAs drained ran up to
   // 15 % slower, leaving the last ones 40 us behind) takes fewer columns.
   // s_next[(kk + 1) & 1] carries the item after `nxt` from thread 0 to the
-  // others across the transforms' barriers.
+  // others across the inverse transform's barriers.
   __shared__ int s_next[2];
   int nxt = vb + vg;  // the item after `it`
   if (ctr) {
@@ -508,7 +508,10 @@ __device__ __forceinline__ void col_main_body(int vb, int vg, Members mem, WsOff
 #pragma unroll 1
   for (int it = vb; it < total; ++kk) {
     if (nxt >= total) grid_dep_trigger();  // last item of this CTA
-    if (ctr && tid == 0) s_next[(kk + 1) & 1] = (nxt < total) ? vg + atomicAdd(ctr, 1) : total;
+    // (thread 0 stores the counter's answer only after the forward transform,
+    // so that its warp does not wait for the atomic at the start of the item)
+    int grabbed = total;
+    if (ctr && tid == 0 && nxt < total) grabbed = vg + atomicAdd(ctr, 1);
     const int mi = it / items, item = it - mi * items;
     cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(member_at(mem, mi), off.A);
     const int col = item * CC + cl;
@@ -565,6 +568,7 @@ __device__ __forceinline__ void col_main_body(int vb, int vg, Members mem, WsOff
         o[m] = o[m] * (valid ? mult_high<GEN>(mt, wx2, kxc, gx, q + 1) : R(0));
       }
     }
+    if (ctr && tid == 0) s_next[(kk + 1) & 1] = grabbed;
     if constexpr (PF)
       if (nxt < total) load_col(nxt, xn);
     // the next item's m1 rows into the other buffer (last read by the item
