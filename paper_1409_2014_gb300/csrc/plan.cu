@@ -412,7 +412,15 @@ static dsnu_status setup_spread(dsnu_plan_s* P, const std::vector<int2>& q0, con
   const bool tune = !(env && env[0] == '0');
   int choice = 0;
   bool have = !tune;
-  if (tune) {
+  // DSNU_SPREAD_CFG=<k> fixes candidate k of kSpreadCfgs (no timing)
+  if (const char* fix = std::getenv("DSNU_SPREAD_CFG")) {
+    const int k = std::atoi(fix);
+    if (k >= 0 && k < kNumSpreadCfgs) {
+      choice = k;
+      have = true;
+    }
+  }
+  if (tune && !have) {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
