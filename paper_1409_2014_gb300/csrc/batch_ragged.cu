@@ -15,8 +15,10 @@
 //     would on the whole grid (the same arithmetic; compiled into another
 //     kernel, where the compiler may contract multiply-adds differently, so a
 //     member's result equals its own dsnu_solve to FP32 rounding);
-//   * interp, spread and spread_reduce take one CTA per (member, block of
-//     nodes / work item / tile), numbered plan by plan.
+//   * interp, spread and spread_reduce take one CTA per (member, interpolation
+//     item / spreading item / tile), numbered plan by plan; the column stage's
+//     CTAs of a plan take its columns from that plan's work counter, as in a
+//     single solve.
 //
 // Every FFT body here uses 256 threads (FP32, transform lengths 256 .. 2048),
 // so one block size serves all plans.  The spreading pair needs one tile
@@ -58,6 +60,9 @@ struct RagGroup {
   const int2* node_q0;
   const float* node_w;
   const double* node_D;
+  const int* itile_ptr;    // the plan's interpolation items (k_interp_tile)
+  const int2* itile_org;
+  const int* itile_nodes;
   int n_nodes, w;
   const int2* item_range;
   const int* ent_node;
@@ -107,7 +112,9 @@ __device__ __forceinline__ int rag_group(const RagTable& T, int s, int b) {
 #define DSNU_RAG_ROWF(L) \
   row_fwd_body<float, L>(vb, vg, a.mem, a.off, a.ldqA, a.ldqB, a.Q, a.ny, a.ax, a.decon_y, 0, a.status)
 #define DSNU_RAG_BANDF(L) band_fwd_body<float, L>(vb, vg, a.mem, a.off, a.ldqB, a.Q + 1, a.ldq, a.Q, a.ay, 0)
-#define DSNU_RAG_COL(L) col_main_body<float, L, false>(vb, vg, a.mem, a.off, a.ldqA, a.nx + 1, a.ay, a.mt, 0, nullptr)
+#define DSNU_RAG_COL(L)                                                                  \
+  col_main_body<float, L, false>(vb, vg, a.mem, a.off, a.ldqA, a.nx + 1, a.ay, a.mt, 0, \
+                                 ws_ptr<int>(member_at(a.mem, 0), a.off.sched))
 #define DSNU_RAG_BANDI(L) band_inv_body<float, L>(vb, vg, a.mem, a.off, a.ldq, a.Q, a.Q + 1, a.ldqB, a.ay, 0)
 #define DSNU_RAG_ROWI(L)                                                                                       \
   row_inv_body<float, L>(vb, vg, a.mem, a.off, a.ldqA, a.ldqB, a.Q, a.ny, a.ax, a.decon_y, a.scale, 0, a.bpf, \
@@ -136,7 +143,8 @@ __global__ void __launch_bounds__(256) k_rag_interp(const __grid_constant__ RagT
   int g, bx, mi;
   rag_numbered(T, RS_INTERP, &g, &bx, &mi);
   const RagGroup& a = T.g[g];
-  interp_body<float>(bx, mi, a.mem, a.off, a.ldq, a.Q, a.node_q0, a.node_w, a.node_D, a.n_nodes, a.w, 0);
+  interp_tile_body<float>(bx, mi, a.mem, a.off, a.ldq, a.Q, a.node_q0, a.node_w, a.node_D, a.itile_ptr, a.itile_org,
+                          a.itile_nodes, a.w, 0);
 }
 
 template <int TILE, int SPLIT, int CHUNK>
@@ -319,6 +327,9 @@ dsnu_status ragged_create(const RaggedGroupIn* groups, int n, Ragged** out) {
     a.node_q0 = t.node_q0;
     a.node_w = static_cast<const float*>(t.node_w);
     a.node_D = t.node_D;
+    a.itile_ptr = t.itile_ptr;
+    a.itile_org = t.itile_org;
+    a.itile_nodes = t.itile_nodes;
     a.n_nodes = g.n_nodes;
     a.w = g.w;
     a.item_range = t.item_range;
@@ -343,7 +354,8 @@ dsnu_status ragged_create(const RaggedGroupIn* groups, int n, Ragged** out) {
     weight[RS_BANDF].push_back(items[RS_BANDF].back() * ly);
     items[RS_BANDI].push_back(items[RS_BANDF].back());
     weight[RS_BANDI].push_back(weight[RS_BANDF].back());
-    T.per[RS_INTERP][i] = (g.n_nodes + 7) / 8;
+    T.per[RS_INTERP][i] = std::max(g.n_itiles, 1);
+    R->smem[RS_INTERP] = std::max(R->smem[RS_INTERP], interp_tile_smem(g.w, sizeof(cpx<float>)));
     T.per[RS_SPREAD][i] = std::max(g.n_items, 1);
     T.per[RS_REDUCE][i] = std::max(g.n_tiles, 1);
     R->smem[RS_ROWF] = std::max(R->smem[RS_ROWF], sx.smem_rowf);
@@ -415,7 +427,7 @@ dsnu_status ragged_enqueue(const Ragged* R, cudaStream_t st) {
   launch_k(pdl, k_rag_col_main, dim3(R->grid[RS_COL]), b, R->smem[RS_COL], st, T);
   cudaStream_t bs = R->side;
   launch_k(pdl, k_rag_band_fwd, dim3(R->grid[RS_BANDF]), b, R->smem[RS_BANDF], bs, T);
-  launch_k(pdl, k_rag_interp, dim3(R->grid[RS_INTERP]), b, 0, bs, T);
+  launch_k(pdl, k_rag_interp, dim3(R->grid[RS_INTERP]), b, R->smem[RS_INTERP], bs, T);
   if (R->spread_cfg >= 0) {
 #define DSNU_RAG_SPREAD(TL, SP, CH)                                                                         \
   launch_k(pdl, k_rag_spread<TL, SP, CH>, dim3(R->grid[RS_SPREAD]), dim3(TL * TL * SP), 0, bs, T);          \

@@ -658,64 +658,20 @@ k_band_fwd(Members mem, WsOff off, int ldqB, int ncols, int ldq, int Q, AxisTabs
 }
 
 // ---------------------------------------------------------------------------
-// Type-2 interpolation: one warp per polar node, gathering from the band
-// array (the stage launches of ragged batches).
-// (bx: the block of 8 nodes, mi: the member)
-template <typename R>
-__device__ __forceinline__ void interp_body(int bx, int mi, Members mem, WsOff off, int ldq, int Q,
-                                            const int2* __restrict__ q0, const R* __restrict__ wts,
-                                            const double* __restrict__ D, int n_nodes, int w, int cj) {
-  grid_dep_wait();
-  const Member mb = member_at(mem, mi);
-  const cpx<R>* __restrict__ Bband = ws_ptr<cpx<R>>(mb, off.Bband);
-  cpx<R>* __restrict__ c = ws_ptr<cpx<R>>(mb, off.c);
-  const int lane = threadIdx.x & 31;
-  const int j = bx * 8 + (threadIdx.x >> 5);
-  if (j >= n_nodes) return;
-  const int2 b0 = q0[j];
-  const R* wx = wts + size_t(j) * 2 * w;
-  const R* wy = wx + w;
-  R ax = R(0), ay = R(0);
-  for (int p = lane; p < w * w; p += 32) {
-    const int b = p / w, a = p - b * w;
-    const int qx = b0.x + a, qy = b0.y + b;
-    cpx<R> v;
-    if (qx >= 0) {
-      v = Bband[size_t(qx) * ldq + qy + Q];
-    } else {
-      v = conj(Bband[size_t(-qx) * ldq + (Q - qy)]);
-    }
-    const int e = qx + qy;
-    v = mul_ipow(v, cj ? -e : e);  // centring phase i^{q_x + q_y}
-    const R f = wx[a] * wy[b];
-    ax += f * v.x;
-    ay += f * v.y;
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    ax += __shfl_xor_sync(0xffffffffu, ax, off);
-    ay += __shfl_xor_sync(0xffffffffu, ay, off);
-  }
-  if (lane == 0) {
-    const double d = D[j];
-    c[j] = mk<R>(R(d * double(ax)), R(d * double(ay)));
-  }
-}
-
-// The interpolation of single plans, by tiles of stencil origins (interp_body,
-// one warp per node gathering straight from the band array, serves the
-// stage launches of ragged batches): the plan groups the
-// nodes by the kItile x kItile tile of the (q_x, q_y) plane that holds their
-// stencil origin, in work items of at most kItileNodes nodes of one tile; one
-// CTA per item copies the (kItile + w - 1)^2 band values
-// its stencils reach into shared memory (whole band columns' runs, read
+// Type-2 interpolation (eq. 2.2) and the polar weighting c_j = D_j rho_hat_j
+// (eq. I2PolarDisc, FP64 multiply), by tiles of stencil origins: the plan
+// groups the nodes by the kItile x kItile tile of the (q_x, q_y) plane that
+// holds their stencil origin, in work items of at most kItileNodes nodes of
+// one tile; one CTA per item copies the (kItile + w - 1)^2 band values its
+// stencils reach into shared memory (whole band columns' runs, read
 // coalesced once; the Hermitian fold for q_x < 0 and the centring phase
 // applied on the way; zero outside the band) and then runs every node's
-// stencil sum from there, four threads per node (the same terms as
-// interp_body, summed in another order).  The band values are read once per
-// item instead of once per stencil that covers them, in runs rather than in
-// scattered 8-byte loads, and a CTA starts all its nodes at once, which is what
-// makes the stage fast on the few SMs it gets next to the column pass.
+// stencil sum from there, four threads per node.  The band values are read
+// once per item instead of once per stencil that covers them, in runs rather
+// than in scattered 8-byte loads (one warp per node gathering them from the
+// band array took 79 us on 12 SMs, against 19 us on 6 for this form), and a CTA
+// starts all its nodes at once, which is what makes the stage fast on the few
+// SMs it gets next to the column pass.
 constexpr int kItile = 32;       // tile edge (stencil origins)
 constexpr int kItileNodes = 64;  // nodes per work item at most (four threads each: 256)
 template <typename R>
