@@ -174,6 +174,39 @@ def test_repeat_calls_bitwise_identical():
     plan.close()
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_results_do_not_depend_on_the_launch_schedule(prec, monkeypatch):
+    """The column pass hands out its columns from a work counter, in the order
+    the CTAs ask for them, and large mixed plans run the band chain next to it
+    on a share of the SMs: which CTA computes a column, and when, must not
+    change a bit of the result.  The same density is solved with programmatic
+    launch on and off (DSNU_PDL) and with the band chain overlapped, in line
+    or on another share of the SMs (DSNU_BAND_SMS); a fixed spreading
+    configuration keeps the spreading's summation order the same in every
+    plan."""
+    from paper_1409_2014_gb300 import Plan
+
+    n = 2048
+    rho = torch.from_numpy(synth.density_abs2(n, n, 32.0, 32.0, 11, 8)).cuda()
+    monkeypatch.setenv("DSNU_SPREAD_CFG", "0")
+    outs = []
+    for pdl, band in (("1", None), ("0", None), ("1", "0"), ("1", "24")):
+        monkeypatch.setenv("DSNU_PDL", pdl)
+        if band is None:
+            monkeypatch.delenv("DSNU_BAND_SMS", raising=False)
+        else:
+            monkeypatch.setenv("DSNU_BAND_SMS", band)
+        plan = Plan(n, lx=32.0, cut_radius=8.0, n_r=64, n_theta=256, precision=prec)
+        for _ in range(2):
+            out = plan.solve(rho)
+        torch.cuda.synchronize()
+        assert plan.status_poll() == 0
+        outs.append(out.clone())
+        plan.close()
+    for o in outs[1:]:
+        assert torch.equal(outs[0], o)
+
+
 def test_solve_host_matches_device():
     from paper_1409_2014_gb300 import Plan
 
