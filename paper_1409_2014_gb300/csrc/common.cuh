@@ -550,6 +550,27 @@ __device__ __forceinline__ double add_f32_f64(float a, float b) {
   return out;
 }
 
+// FP64 -> FP32, rounded to nearest with ties to even, by integer instructions.
+// For a double whose rounded value is a normal float, or that is a zero: the
+// exponent is rebiased (1023 -> 127) and the top 23 fraction bits kept, which
+// is the value truncated toward zero; adding 1 when the first dropped bit is
+// set and either a later dropped bit or the kept last bit is set rounds it to
+// nearest, ties to even (a carry out of the fraction steps the exponent, up to
+// the infinity pattern past the largest float, as the rounding does).  `odd`
+// is set for the other doubles (subnormal or too small results, infinities,
+// NaNs, magnitudes from 2^128 up), which the caller converts with the hardware
+// instruction, out of line (f32_of_f64_hw).
+__device__ __forceinline__ float f32_of_f64_int(double d, bool& odd) {
+  const unsigned hi = unsigned(__double2hiint(d)), lo = unsigned(__double2loint(d));
+  const unsigned ha = hi & 0x7FFFFFFFu;
+  unsigned f = __funnelshift_l(lo, ha - 0x38000000u, 3);  // exponent - 896, 20 + 3 fraction bits
+  f += ((lo >> 28) & 1u) & ((((lo & 0x0FFFFFFFu) != 0u) ? 1u : 0u) | (f & 1u));
+  const bool zero = (ha | lo) == 0u;
+  odd = !zero && (ha - 0x38100000u > 0x47EFFFFFu - 0x38100000u);
+  return __uint_as_float((zero ? 0u : f) | (hi & 0x80000000u));
+}
+static __device__ __noinline__ float f32_of_f64_hw(double d) { return __double2float_rn(d); }
+
 // expm1 in the working precision (library function).
 template <typename R>
 __device__ __forceinline__ R expm1_r(R x) {

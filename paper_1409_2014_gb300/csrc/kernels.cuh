@@ -348,12 +348,38 @@ __device__ __forceinline__ void row_fwd_body(int vb, int vg, Members mem, WsOff 
       landed = mbar_wait(bar, phase, 1000000000ull);
       phase ^= 1u;
     }
+    // FP32 with the landing buffer: rho rounded to FP32, half of the 16 values
+    // by the conversion instruction and half by integer instructions
+    // (f32_of_f64_int, the same result bit for bit): the instruction runs on
+    // GB300's narrow FP64 pipe, the integer form on the integer pipe, and the
+    // two halves overlap (all by the instruction cost this pass 19 us, all by
+    // integers about as much; half and half 15 us).  One vote of the warp
+    // sends the rare values outside the integer form's range to the
+    // instruction, out of line.
+    R xs[PF ? 16 : 1];
+    if constexpr (PF) {
+      unsigned oddm = 0u;
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        if (m & 1) {
+          bool odd;
+          xs[m] = f32_of_f64_int(land[rr * GG::LS + t + G * m], odd);
+          oddm |= (odd && valid) ? (1u << m) : 0u;
+        } else {
+          xs[m] = __double2float_rn(land[rr * GG::LS + t + G * m]);
+        }
+      }
+      if (__any_sync(0xffffffffu, oddm != 0u)) {
+        for (int m = 1; m < 16; m += 2)
+          if ((oddm >> m) & 1u) xs[m] = f32_of_f64_hw(land[rr * GG::LS + t + G * m]);
+      }
+    }
     cpx<R> e[16], o[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
       const int n = t + G * m;
       R x;
-      if constexpr (PF) x = valid ? from_f64<R>(land[rr * GG::LS + n]) : R(0);
+      if constexpr (PF) x = valid ? xs[m] : R(0);
       else x = valid ? from_f64<R>(rho[size_t(row) * N + n]) : R(0);
       const cpx<R> z = mk<R>(x, isg * (x * ax.decon[n] * dy));
       cpx<R> w;
