@@ -624,20 +624,25 @@ def run_ours(args):
     # ---- end to end through the public API with host buffers: every step copies its
     # density from pinned host memory and its potential back (dsnu_solve_host_stream,
     # uploads and downloads overlapped with the neighbouring steps' solves)
+    # (at least 60 solves per run, so that filling and draining the copy
+    # pipeline is a small part; three runs, the median reported: a host link
+    # shared with other jobs dips now and then)
     rho_h = torch.from_numpy(rho_np).pin_memory()
     phi_h = torch.empty_like(rho_h).pin_memory()
-    ke = max(3, min(args.steps, 100))
+    ke = max(60, min(args.steps, 200))
     plan.solve_host_stream([rho_h, rho_h], [phi_h, phi_h])
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    plan.solve_host_stream([rho_h] * ke, [phi_h] * ke)
-    e1.record(stream)
-    barrier()
-    te = max_time(e0.elapsed_time(e1) / 1000.0)
-    e2e = {"value": world * ke / te, "unit": "solves/s", "h2d_bytes_per_step": int(rho_h.numel() * 8),
-           "d2h_bytes_per_step": int(phi_h.numel() * 8), "steps": ke,
+    runs = []
+    for _ in range(3):
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.solve_host_stream([rho_h] * ke, [phi_h] * ke)
+        e1.record(stream)
+        barrier()
+        runs.append(world * ke / max_time(e0.elapsed_time(e1) / 1000.0))
+    e2e = {"value": float(np.median(runs)), "unit": "solves/s", "h2d_bytes_per_step": int(rho_h.numel() * 8),
+           "d2h_bytes_per_step": int(phi_h.numel() * 8), "steps": ke, "runs": runs,
            "api": "dsnu_solve_host_stream (pinned host in/out, copies overlapped with solves)"}
     phi_e2e = phi_h.numpy().copy()
     assert np.array_equal(phi_e2e, phi_mixed), "streamed host solve differs from the device solve"
