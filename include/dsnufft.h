@@ -47,7 +47,7 @@ typedef enum {
   DSNU_ENOMEM = 2,        /* a plan table allocation failed */
   DSNU_ECUDA = 3,         /* a CUDA runtime call failed; see dsnu_last_error() */
   DSNU_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
-  DSNU_EUNSUPPORTED = 5   /* valid request outside what this build supports */
+  DSNU_EUNSUPPORTED = 5   /* valid request outside what the library supports */
 } dsnu_status;
 
 typedef enum {

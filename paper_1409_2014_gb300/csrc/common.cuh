@@ -465,7 +465,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 }
 
 // The way out of a prefetching loop after a bounded wait expired in some
-// thread of the CTA (every thread calls it, with that thread's verdict): the
+// thread of the CTA (every thread calls it, with its own wait's outcome): the
 // status word records the timeout, thread 0 waits (bounded again) for the copy
 // still in flight on phase `parity` of `bar`, so that the CTA does not exit
 // while data lands in its shared memory, and the caller returns without
