@@ -513,21 +513,18 @@ __device__ __forceinline__ void col_main_body(int vb, int vg, Members mem, WsOff
     for (int m = 0; m < (PF ? 16 : 1); ++m)
       x[m] = (col2 < ncols) ? A2[Tile<R>::at(t + G * m, col2, ldqA)] : mk<R>(R(0), R(0));
   };
-  // Items: CTA vb starts with item vb; with a work counter (`ctr`, zeroed by
-  // the row pass before) each CTA then takes the next free item, item vg + c
-  // for the counter's value c, else items vb + vg, vb + 2 vg, ...  Taken from
-  // a counter, a CTA that runs slower than the others (persistent CTAs that a
-  // programmatic launch placed as the previous kernel's CTAs drained ran up to
-  // 15 % slower, leaving the last ones 40 us behind) takes fewer columns.
-  // s_next[(kk + 1) & 1] carries the item after `nxt` from thread 0 to the
-  // others across the inverse transform's barriers.
+  // Items: CTA vb starts with items vb and vb + vg; with a work counter
+  // (`ctr`, zeroed by the row pass before) each CTA then takes the next free
+  // item, item 2 vg + c for the counter's value c, else items vb + 2 vg,
+  // vb + 3 vg, ...  Taken from a counter, a CTA that runs slower than the
+  // others (persistent CTAs that a programmatic launch placed as the previous
+  // kernel's CTAs drained ran up to 15 % slower, leaving the last ones 40 us
+  // behind) takes fewer columns; the first two items need no atomic, so the
+  // first answer is ready within the first item.  s_next[(kk + 1) & 1]
+  // carries the item after `nxt` from thread 0 to the others across the
+  // inverse transform's barriers.
   __shared__ int s_next[2];
   int nxt = vb + vg;  // the item after `it`
-  if (ctr) {
-    if (tid == 0) s_next[0] = (vb < total) ? vg + atomicAdd(ctr, 1) : total;
-    __syncthreads();
-    nxt = s_next[0];
-  }
   if constexpr (PF)
     if (vb < total) load_col(vb, xn);
   int kk = 0;  // items done by this CTA (the multiplier buffer is kk & 1)
@@ -537,7 +534,7 @@ __device__ __forceinline__ void col_main_body(int vb, int vg, Members mem, WsOff
     // (thread 0 stores the counter's answer only after the forward transform,
     // so that its warp does not wait for the atomic at the start of the item)
     int grabbed = total;
-    if (ctr && tid == 0 && nxt < total) grabbed = vg + atomicAdd(ctr, 1);
+    if (ctr && tid == 0 && nxt < total) grabbed = 2 * vg + atomicAdd(ctr, 1);
     const int mi = it / items, item = it - mi * items;
     cpx<R>* __restrict__ A = ws_ptr<cpx<R>>(member_at(mem, mi), off.A);
     const int col = item * CC + cl;
