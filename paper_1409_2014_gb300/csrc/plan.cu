@@ -869,16 +869,20 @@ dsnu_status dsnu_plan_create_multiplier(const dsnu_params* params, const dsnu_mu
   }
   layout_workspace(P);
   // mixed plans on large grids: the band chain runs next to the column pass
-  // on a low-priority side stream, the column pass leaving 16 of every 152 SMs
-  // free (measured best at 4096^2 on GB300 over 0..24 SMs, with the column
-  // pass's work counter and the tiled interpolation: 0.5137 ms against
-  // 0.5226 with 12 and 0.534 with the band chain in line);
+  // on a low-priority side stream, the column pass leaving it 16 of every 152
+  // SMs at 4096^2 and a share growing as 1/sqrt(nx ny) for smaller grids,
+  // whose band chain (its node work is the same) is larger next to their
+  // column pass: measured best on GB300 16 SMs at 4096^2 (0.5137 ms against
+  // 0.5226 with 12 and 0.534 with the band chain in line) and 32 at 2048^2
+  // (0.131-0.134 ms against 0.139 with 16 and 0.150 in line);
   // DSNU_BAND_SMS=<n> sets the number of SMs, 0 turns it off
   if (p.precision == DSNU_MIXED && !standard) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int reserve = (p.nx >= 2048 && p.ny >= 2048) ? std::max(1, (sms * 16 + 76) / 152) : 0;
+    int reserve = 0;
+    if (p.nx >= 2048 && p.ny >= 2048)
+      reserve = std::max(1, int(std::lround(sms * (16.0 / 152.0) * 4096.0 / std::sqrt(double(p.nx) * p.ny))));
     const char* env = std::getenv("DSNU_BAND_SMS");
     if (env) reserve = std::atoi(env);
     if (reserve > 0) {
